@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark of the collision-operator hot path on GB300.
+
+One step = one evaluation of Q(f, f) (reconstruction, loss sums, fused point
+generation + spreading, cosine transform + deconvolution, combine) for the 2D
+hard-sphere workload: d = 2, N = 64 (65^2 modes), M = 32 circle points, S = 3,
+gamma = 1, algebraic map, f = three Maxwellians + a Gaussian-windowed positive
+perturbation (seeded synthetic input, projected on the GPU).  The headline arm is
+the FP32-spreading path (tol 1e-6, FP64 loss / transform / deconvolution); the
+FP64-spreading path is timed beside it.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Q(f,f) evals/s and NU points/s at stated rel err; FP32/batched vs FP64, % roofline"
+UNIT = "Q evals/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int, enabled: bool = True):
+        self.enabled = enabled
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        if not self.enabled:
+            return self
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.enabled or self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------- distributed
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(workload, budget_s=12.0):
+    """FP64 oracle, as it stands, on a bounded sample: the first n outer nodes i of the
+    workload's triple sum (all j, all sigma_m, all modes); extrapolated to one evaluation."""
+    from oracle import oracle as O
+
+    d, N, M, S, g = workload.d, workload.N, workload.M, workload.S, workload.gamma
+    ft = O.project(workload, d, N, S, 1).ravel()
+    nnode = N ** d
+    threads = O.default_threads()
+    n = max(threads, 8)
+    t0 = time.perf_counter()
+    O.collide_parts(ft, d, N, M, S, g, r=1, outer=(0, n), nthreads=threads)
+    dt = time.perf_counter() - t0
+    per_node = dt / n
+    n2 = int(min(nnode, max(n, budget_s / per_node)))
+    n2 = max(threads, (n2 // threads) * threads)
+    t0 = time.perf_counter()
+    O.collide_parts(ft, d, N, M, S, g, r=1, outer=(0, n2), nthreads=threads)
+    dt2 = time.perf_counter() - t0
+    evals_per_s = (n2 / nnode) / dt2
+    return {"value": evals_per_s, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"outer nodes 0..{n2 - 1} of {nnode} (all j, all {M} sigma, all {(N + 1) ** d} modes) "
+                      f"in {dt2:.2f} s, scaled by {nnode}/{n2}"}
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+
+    from paper_2105_08806_gb300 import PG_PREC_FP32, PG_PREC_FP64, Plan
+    from paper_2105_08806_gb300 import workloads as Wl
+    from paper_2105_08806_gb300.build import build
+
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build()
+    w = Wl.c2_2d_vhs()
+    d, N, M, S, gamma = w.d, w.N, w.M, w.S, w.gamma
+    stream = torch.cuda.Stream(device=dev)
+    plan32 = Plan(d, N, M, S, gamma, 1e-6, precision=PG_PREC_FP32)
+    plan64 = Plan(d, N, M, S, gamma, 1e-13, precision=PG_PREC_FP64)
+    for p in (plan32, plan64):
+        p.set_stream(stream)
+    info32, info64 = plan32.info(), plan64.info()
+
+    # input: f at the projection nodes (seeded workload density), projected on the GPU
+    import numpy as np
+    v = np.array(plan32.project_nodes())
+    grids = np.meshgrid(*([v] * d), indexing="ij")
+    fv = torch.as_tensor(w(np.stack([g.ravel() for g in grids], 1)), device=dev)
+    ft = torch.empty((N + 1) ** d, dtype=torch.float64, device=dev)
+    Q = torch.empty_like(ft)
+    Q64 = torch.empty_like(ft)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > 129 MB L2
+    with torch.cuda.stream(stream):
+        plan32.project(fv, ft)
+    stream.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed_loop(plan, out, steps, warmup):
+        for _ in range(warmup):
+            plan.collide(ft, out)
+        stream.synchronize()
+        plan.set_timing(True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        stages = []
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+            evs[k][0].record(stream)
+            plan.collide(ft, out)
+            evs[k][1].record(stream)
+            stages.append(plan.stage_times())
+        barrier()
+        wall = time.perf_counter() - t0
+        plan.set_timing(False)
+        ms = [a.elapsed_time(b) for a, b in evs]
+        return ms, stages, wall
+
+    with ClockSampler(local, enabled=not args.no_clocks) as clk:
+        ms32, st32, wall32 = timed_loop(plan32, Q, args.steps, args.warmup)
+    clocks = clk.summary()
+    ms64, st64, _ = timed_loop(plan64, Q64, max(1, args.fp64_steps), 1)
+
+    # end to end through the public API: pinned host f~ in, host Q out, every step
+    fh = ft.cpu().pin_memory()
+    qh = torch.empty_like(fh).pin_memory()
+    fd = torch.empty_like(ft)
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        with torch.cuda.stream(stream):
+            fd.copy_(fh, non_blocking=True)
+        plan32.collide(fd, Q)
+        with torch.cuda.stream(stream):
+            qh.copy_(Q, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(a.elapsed_time(b))
+
+    mean32 = statistics.mean(ms32)
+    mean_e2e = statistics.mean(e2e_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([mean32, mean_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        mean32, mean_e2e = float(t[0]), float(t[1])
+    err = float(torch.linalg.norm(Q - Q64) / torch.linalg.norm(Q64))
+    mom = plan64.moments()
+
+    # roofline of the dominant kernel (spreading): shared-memory read-modify-writes
+    spread_ms = statistics.mean(s[2] for s in st32)
+    wgt = info32["kernel_width"]
+    rmw_per_launch = info32["points"] * wgt ** d
+    props = torch.cuda.get_device_properties(dev)
+    sm_count = props.multi_processor_count
+    peak_rmw = sm_count * 32 * 2.07e9  # one 32-lane shared-memory access per SM per clock at 2070 MHz
+    achieved = rmw_per_launch / (spread_ms * 1e-3)
+    stage_names = ["reconstruct", "loss", "spread", "transform"]
+    stage_mean32 = {n: statistics.mean(s[i] for s in st32) for i, n in enumerate(stage_names)}
+    stage_mean64 = {n: statistics.mean(s[i] for s in st64) for i, n in enumerate(stage_names)}
+
+    value = world * 1000.0 / mean32
+    res = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": mean32,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded three-Maxwellian + perturbation density, projected on the GPU)",
+        "config": {
+            "workload": "2D hard spheres (gamma=1), N=64 (65^2 modes), M=32 circle points, S=3, algebraic map",
+            "spread_precision": "fp32 (tol 1e-6); loss, transform, deconvolution fp64",
+            "kernel_width": wgt, "n_grid": info32["n_grid"], "n_fold": info32["n_fold"],
+            "points_per_eval": info32["points"], "spread_blocks": info32["spread_blocks"],
+            "l2": "flushed between timed steps (256 MiB write, outside the step events)",
+            "parallelism": f"replicas x{world} (independent evaluations, no collective)",
+        },
+        "points_per_s": value * info32["points"],
+        "points_per_s_paper_convention": value * M * (N + 2) ** (2 * d),
+        "rel_err_fp32_vs_fp64_path": err,
+        "fp64_path": {"value": 1000.0 / statistics.mean(ms64), "ms_per_step": statistics.mean(ms64),
+                      "steps": len(ms64), "kernel_width": info64["kernel_width"], "stages_ms": stage_mean64},
+        "speedup_fp32_vs_fp64": statistics.mean(ms64) / mean32,
+        "stages_ms": stage_mean32,
+        "conservation_fp64": {"mass_rel": abs(mom["mass"]) / abs(mom["mass_gain"]),
+                              "energy_rel": abs(mom["energy"]) / abs(mom["energy_gain"])},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_rmw / 1e9,
+                     "unit": "G shared-memory RMW/s", "frac": achieved / peak_rmw, "traffic": None,
+                     "kernel": "k_spread<float,2,%d>" % wgt,
+                     "peak_basis": f"{sm_count} SMs x 32 shared-memory lanes/clk x 2070 MHz (derived)"},
+        "e2e": {"value": world * 1000.0 / mean_e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * (N + 1) ** d,
+                "d2h_bytes_per_step": 8 * (N + 1) ** d},
+        "gpu_launches": info32["launches_per_collide"] * args.steps,
+        "clocks": clocks,
+        "wall_s_timed_region": wall32,
+    }
+    plan32.close()
+    plan64.close()
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------- reference arm
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2105_08806_gb300 import workloads as Wl
+
+    w = Wl.c2_2d_vhs()
+    d, N, M, S, g = w.d, w.N, w.M, w.S, w.gamma
+    ft = O.project(w, d, N, S, 1).ravel()
+    nnode = N ** d
+    threads = O.default_threads()
+    n = threads  # outer nodes per sampled step
+    times = []
+    for k in range(args.warmup + args.steps):
+        lo = (k * n) % nnode
+        t0 = time.perf_counter()
+        O.collide_parts(ft, d, N, M, S, g, r=1, outer=(lo, min(nnode, lo + n)), nthreads=threads)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    step_s = statistics.mean(times)
+    value = (n / nnode) / step_s
+    res = {
+        "impl": "reference",
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "2D hard spheres (gamma=1), N=64 (65^2 modes), M=32 circle points, S=3, algebraic map",
+                   "implementation": "FP64 CPU oracle (direct triple sum), host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"each step: {n} outer nodes of {nnode} (all j, sigma, modes), scaled by {nnode}/{n}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(res))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

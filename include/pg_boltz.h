@@ -1,0 +1,179 @@
+/*
+ * pg_boltz.h -- C ABI of the GB300 (sm_103a) library that evaluates the
+ * Petrov-Galerkin mapped-Chebyshev collision operator of arXiv 2105.08806
+ * with the fast (non-uniform FFT) algorithm of its Section 4.2.
+ *
+ * The operator (Section 3, Eq. Qk_component, discretised as in Section 4):
+ *
+ *   Q_k = sum_{i,j} sum_m W_i W_j w_m B(|v_i - v_j|) g_i g_j [That_k(v'_ijm) - That_k(v_i)],
+ *   0 <= k_l <= N,  l = 1..d,
+ *
+ * over the N interior Chebyshev-Gauss-Lobatto nodes per axis of M_v = N + 2
+ * (Section 4.2), with g_i = f_N(v_i)/mu(xi_i)^2, v' = (v_i+v_j)/2 + |v_i-v_j| sigma_m/2,
+ * That_k the test functions of Eq. 1DCheby and B = |g|^gamma / |S^{d-1}| (VHS,
+ * Section 3.1).  The gain sum is evaluated as a type-1 non-uniform cosine
+ * transform (Eq. num_fast_k, Eq. nufft): exponential-of-semicircle spreading onto
+ * a folded, oversampled cosine grid, a d-dimensional cosine transform and a
+ * deconvolution; the loss is Eq. Qminus.
+ *
+ * Conventions for every entry point:
+ *  - Arrays of modes are (N+1)^d doubles in C order over (k_1, ..., k_d),
+ *    k_d fastest.  "Device" pointers are CUDA global-memory pointers of the
+ *    current device; "host" pointers are ordinary host memory.
+ *  - Return codes: PG_OK (0) or a negative PG_ERR_* code; functions returning a
+ *    pointer return NULL on failure.  pg_boltz_last_error() (thread-local) then
+ *    holds a one-line reason.  No function aborts, prints or exits.
+ *  - A plan owns every device buffer it allocates and is freed by
+ *    pg_boltz_destroy.  Caller arrays stay owned by the caller.
+ *  - A plan is not thread-safe: use one plan per host thread / stream.
+ *  - Work is enqueued on the plan's stream (default: the legacy default
+ *    stream) and the calls return after enqueue, except where noted.
+ */
+#ifndef PG_BOLTZ_H
+#define PG_BOLTZ_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define PG_OK 0
+#define PG_ERR_ARG (-1)     /* invalid argument or NULL handle            */
+#define PG_ERR_NOMEM (-2)   /* host or device allocation failed           */
+#define PG_ERR_CUDA (-3)    /* a CUDA runtime call or launch failed       */
+#define PG_ERR_TIMEOUT (-4) /* a bounded device-side wait gave up         */
+#define PG_ERR_STATE (-5)   /* call not valid in the plan's current state */
+
+/* Arithmetic of the spreading stage. */
+#define PG_PREC_AUTO 0 /* tol < 1e-8 -> FP64, else FP32                          */
+#define PG_PREC_FP64 1 /* FP64 point generation, spreading and transform         */
+#define PG_PREC_FP32 2 /* FP32 point generation and shared-memory spreading;
+                          FP64 global grid, cosine transform, deconvolution, loss */
+
+/* Sphere quadrature for d = 3 (d = 2 always uses M uniform polar angles, Section 4.1). */
+#define PG_SPHERE_AUTO 0      /* antipodal Fibonacci set (M even)                  */
+#define PG_SPHERE_ANTIPODAL 1 /* M/2 golden-angle points and their negatives       */
+#define PG_SPHERE_FIBONACCI 2 /* plain M-point golden-angle set                    */
+
+typedef struct pg_boltz_plan_s pg_boltz_plan_t;
+
+/* Extended plan options.  Zero-initialise, then set d, N, M, S, kernel_gamma, tol. */
+typedef struct {
+    int d;               /* velocity dimension, 2 or 3                                   */
+    int N;               /* highest mode per axis (modes 0..N), N >= 2                   */
+    int M;               /* sphere points M_sigma, M >= 2 and even                       */
+    double S;            /* map scale S > 0 (Eq. 1D_mapping)                             */
+    double kernel_gamma; /* VHS exponent, 0 <= gamma <= 1 (Section 3.1)                  */
+    double tol;          /* requested transform precision, 1e-15 <= tol <= 1e-2          */
+    int map_log;         /* 0: algebraic map r = 1 (default); 1: logarithmic map r = 0
+                            (Section 2.1 Remark)                                          */
+    int precision;       /* PG_PREC_*                                                    */
+    int sphere;          /* PG_SPHERE_*                                                  */
+    double upsampfac;    /* grid oversampling sigma, 0 -> 2.0, range [1.5, 4]             */
+    int proj_nodes;      /* Chebyshev-Gauss nodes per axis for pg_boltz_project, 0 -> 4(N+1) */
+    int spread_threads;  /* threads per spreading block, 0 -> automatic                  */
+    int spread_blocks_per_sm; /* spreading blocks per SM, 0 -> automatic                 */
+} pg_boltz_opts_t;
+
+/* Read-only description of a plan (pg_boltz_info). */
+typedef struct {
+    int d, N, M, r, precision, sphere;
+    double S, kernel_gamma, tol, upsampfac;
+    int n_grid;            /* periodic oversampled grid size n (even)                      */
+    int n_fold;            /* folded cosine grid cells per axis, n/2 + 1                    */
+    int kernel_width;      /* spreading kernel width w (grid cells)                         */
+    double kernel_beta;    /* exponential-of-semicircle shape parameter                     */
+    int slabs;             /* shared-memory slabs of the folded grid along axis 1           */
+    int spread_blocks, spread_threads;
+    size_t spread_smem_bytes;
+    long long points;      /* non-uniform points per evaluation, M N^(2d)                   */
+    long long pairs;       /* node pairs per evaluation, N^(2d)                             */
+    int proj_nodes;
+    int launches_per_collide; /* kernels + memsets enqueued by one pg_boltz_collide          */
+    size_t device_bytes;   /* device memory owned by the plan                               */
+} pg_boltz_info_t;
+
+/*
+ * Create a plan with the defaults: algebraic map (r = 1), M_v = N + 2 CGL
+ * nodes (Section 4.2), uniform circle (d = 2) or antipodal Fibonacci sphere
+ * (d = 3), oversampling 2, precision chosen from tol (PG_PREC_AUTO).
+ * Uploads all tables and allocates the workspace on the current device.
+ * Returns NULL on error (PG_ERR_ARG / PG_ERR_NOMEM / PG_ERR_CUDA in last_error).
+ */
+pg_boltz_plan_t *pg_boltz_plan(int d, int N, int M, double S, double kernel_gamma, double tol);
+
+/* Same as pg_boltz_plan with every option of pg_boltz_opts_t. */
+pg_boltz_plan_t *pg_boltz_plan_ex(const pg_boltz_opts_t *opts);
+
+/* Set the CUDA stream (a cudaStream_t, NULL = legacy default stream) for later calls. */
+int pg_boltz_set_stream(pg_boltz_plan_t *plan, void *cuda_stream);
+
+/*
+ * Q_k for the coefficients f~_k of f_N (Eq. fN_Expansion, Section 4.2 fast algorithm).
+ * f_dev, Q_dev: caller-owned device arrays of (N+1)^d doubles (C order); they must not
+ * overlap.  Asynchronous on the plan's stream.  The plan's workspace is reused by the
+ * next call on the same plan, so calls on one plan must not overlap in time.
+ */
+int pg_boltz_collide(pg_boltz_plan_t *plan, const double *f_dev, double *Q_dev);
+
+/*
+ * FP64 diagnostics of the last pg_boltz_collide, copied to host (synchronises the
+ * plan's stream).  out_host[0..5]:
+ *   [0] sum_k a_k Q_k, [1] sum_k b_k Q_k  where 1 = sum a_k That_k, |v|^2 = sum b_k That_k
+ *       (Section 3.3 proof; exact identities for r = 1, N >= 2: mass and energy of Q),
+ *   [2] sum_k a_k Q+_k, [3] sum_k b_k Q+_k (the same functionals of the gain term),
+ *   [4] ||Q||_2, [5] ||Q+||_2.
+ */
+int pg_boltz_moments(pg_boltz_plan_t *plan, double *out_host);
+
+/*
+ * Per-stage timing of pg_boltz_collide (no counterpart in the paper, which reports
+ * whole-evaluation CPU seconds in Section 5.1.1 Test 04).  enable != 0 makes every later
+ * collide record CUDA events on the plan's stream between its stages; 0 stops it.
+ * Creates the events on first use.  Returns PG_OK / PG_ERR_ARG / PG_ERR_CUDA.
+ */
+int pg_boltz_set_timing(pg_boltz_plan_t *plan, int enable);
+
+/*
+ * Durations in milliseconds of the stages of the last timed collide (waits for it):
+ *   ms_out[0] reconstruction of f_N at the nodes, [1] loss sums,
+ *   [2] grid clear + spreading, [3] cosine transform, deconvolution, loss transform, combine.
+ * PG_ERR_STATE if no collide ran since timing was enabled.
+ */
+int pg_boltz_stage_times(pg_boltz_plan_t *plan, double *ms_out);
+
+/*
+ * Velocities v(xi_p) of the proj_nodes Chebyshev-Gauss projection nodes
+ * xi_p = -cos((2p-1) pi / (2 Mp)), p = 1..Mp, written to v_host[0..Mp-1].
+ * *count_out receives Mp.  Host-only, no device work.
+ */
+int pg_boltz_project_nodes(const pg_boltz_plan_t *plan, double *v_host, int *count_out);
+
+/*
+ * f~_k = (f, That_k) (Eq. MultiD_spectral_coef) by Chebyshev-Gauss quadrature.
+ * fvals_dev: device array of Mp^d doubles, f at the tensor grid of the projection
+ * nodes (C order); ftilde_dev: device array of (N+1)^d doubles.  Asynchronous.
+ */
+int pg_boltz_project(pg_boltz_plan_t *plan, const double *fvals_dev, double *ftilde_dev);
+
+/* Describe the plan (host-only). */
+int pg_boltz_info(const pg_boltz_plan_t *plan, pg_boltz_info_t *out);
+
+/* Free the plan and its device memory.  NULL-safe.  Synchronises the plan's stream. */
+void pg_boltz_destroy(pg_boltz_plan_t *plan);
+
+/*
+ * Host-side fault injection for tests: the countdown-th device allocation made by a
+ * later plan creation fails with PG_ERR_NOMEM (0 disables).  Process-wide; no device work.
+ */
+void pg_boltz_debug_fail_alloc(int countdown);
+
+/* Thread-local text of the last error ("" when none); valid until the next call. */
+const char *pg_boltz_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PG_BOLTZ_H */

@@ -57,7 +57,8 @@ def _lib():
     ip = ctypes.POINTER(ctypes.c_int)
     common = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_int, dp, dp,
               ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double]
-    lib.pgb_oracle_collide.argtypes = common + [ctypes.c_int, ip, dp, dp, ctypes.c_int]
+    lib.pgb_oracle_collide.argtypes = common + [ctypes.c_int, ip, ctypes.c_long, ctypes.c_long, dp, dp,
+                                                ctypes.c_int]
     lib.pgb_oracle_collide.restype = ctypes.c_int
     lib.pgb_oracle_weak.argtypes = common + [ctypes.c_int, ip, dp, ctypes.c_int]
     lib.pgb_oracle_weak.restype = ctypes.c_int
@@ -289,14 +290,20 @@ class Problem:
                 _dp(self.wsig), self.S, self.r, self.gamma, self.Bconst)
 
 
-def collide_parts(ftilde, d, N, M, S, gamma, r=1, sphere="auto", modes=None, nthreads=None):
-    """(gain, loss) for the requested modes (default: all (N+1)^d, C-order)."""
+def collide_parts(ftilde, d, N, M, S, gamma, r=1, sphere="auto", modes=None, nthreads=None,
+                  outer=None):
+    """(gain, loss) for the requested modes (default: all (N+1)^d, C-order).
+
+    `outer` = (i_lo, i_hi) restricts the outer node sum to i_lo <= i < i_hi (C-order node
+    index); the default is every node.
+    """
     pb = Problem(ftilde, d, N, M, S, gamma, r, sphere)
     modes = all_modes(d, N) if modes is None else np.ascontiguousarray(np.asarray(modes, dtype=np.int32))
     nm = modes.shape[0]
     gain = np.zeros(nm)
     loss = np.zeros(nm)
-    rc = _lib().pgb_oracle_collide(*pb._common(), nm, _ip(modes), _dp(gain), _dp(loss),
+    i_lo, i_hi = outer if outer is not None else (0, N ** d)
+    rc = _lib().pgb_oracle_collide(*pb._common(), nm, _ip(modes), int(i_lo), int(i_hi), _dp(gain), _dp(loss),
                                    int(nthreads or default_threads()))
     if rc != 0:
         raise RuntimeError(f"pgb_oracle_collide failed: {rc}")

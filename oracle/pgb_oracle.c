@@ -164,20 +164,20 @@ static void *worker(void *arg)
     return NULL;
 }
 
-static int run(prob_t *p, int nthreads, double *gain, double *lossw, double *wk)
+static int run(prob_t *p, long i_lo, long i_hi, int nthreads, double *gain, double *lossw, double *wk)
 {
-    long nnode = 1;
-    for (int l = 0; l < p->d; ++l) nnode *= p->Nn;
+    long span = i_hi - i_lo;
+    if (span < 1) return 0;
     if (nthreads < 1) nthreads = 1;
-    if (nthreads > nnode) nthreads = (int)nnode;
+    if (nthreads > span) nthreads = (int)span;
     pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
     work_t *ws = (work_t *)calloc((size_t)nthreads, sizeof(work_t));
     if (!th || !ws) { free(th); free(ws); return -2; }
     int rc = 0;
     for (int t = 0; t < nthreads; ++t) {
         ws[t].p = p;
-        ws[t].i_begin = (int)(nnode * t / nthreads);
-        ws[t].i_end = (int)(nnode * (t + 1) / nthreads);
+        ws[t].i_begin = (int)(i_lo + span * t / nthreads);
+        ws[t].i_end = (int)(i_lo + span * (t + 1) / nthreads);
         ws[t].gain = (double *)calloc((size_t)(p->nmodes > 0 ? p->nmodes : 1), sizeof(double));
         ws[t].wk = (double *)calloc((size_t)(2 * (p->nphi > 0 ? p->nphi : 1)), sizeof(double));
         ws[t].lossw = lossw;  /* disjoint rows per thread */
@@ -201,12 +201,15 @@ static int run(prob_t *p, int nthreads, double *gain, double *lossw, double *wk)
  * Gain and loss parts of Q_k for the requested modes.
  *   gain[t] = sum_{i,j,m} qbar That_{k_t}(v')                       (Eq. Qplus, discretised)
  *   loss[t] = sum_i That_{k_t}(v_i) * sum_{j,m} qbar                (Eq. Qminus, discretised)
+ * The outer sum runs over the node indices i_lo <= i < i_hi (the full operator when
+ * i_lo = 0, i_hi = Nn^d; a partial range is a bounded sample of the same work).
  * Returns 0, or -1 on bad arguments, -2 when memory runs out.
  */
 int pgb_oracle_collide(int d, int Nn, const double *v1d, const double *g, double Wnode,
                        int M, const double *sig, const double *wsig,
                        double S, int r, double gamma, double Bconst,
-                       int nmodes, const int *modes, double *gain, double *loss, int nthreads)
+                       int nmodes, const int *modes, long i_lo, long i_hi,
+                       double *gain, double *loss, int nthreads)
 {
     if (d < 1 || d > ORACLE_MAX_D || Nn < 1 || M < 1 || nmodes < 1 || (r != 0 && r != 1)) return -1;
     prob_t p;
@@ -220,13 +223,14 @@ int pgb_oracle_collide(int d, int Nn, const double *v1d, const double *g, double
     for (int l = 0; l < d; ++l) nnode *= Nn;
     double *lossw = (double *)calloc((size_t)nnode, sizeof(double));
     if (!lossw) return -2;
+    if (i_lo < 0 || i_hi > nnode || i_lo > i_hi) { free(lossw); return -1; }
     memset(gain, 0, sizeof(double) * (size_t)nmodes);
-    int rc = run(&p, nthreads, gain, lossw, NULL);
+    int rc = run(&p, i_lo, i_hi, nthreads, gain, lossw, NULL);
     if (rc == 0) {
         double *tab = (double *)malloc(sizeof(double) * (size_t)d * (p.kmax + 1));
         double vi[ORACLE_MAX_D];
         memset(loss, 0, sizeof(double) * (size_t)nmodes);
-        for (long i = 0; i < nnode; ++i) {
+        for (long i = i_lo; i < i_hi; ++i) {
             node_coords(&p, i, vi);
             for (int l = 0; l < d; ++l) that_1d(vi[l], S, r, p.kmax, tab + (size_t)l * (p.kmax + 1));
             for (int t = 0; t < nmodes; ++t) {
@@ -262,7 +266,7 @@ int pgb_oracle_weak(int d, int Nn, const double *v1d, const double *g, double Wn
     double *lossw = (double *)calloc((size_t)nnode, sizeof(double));
     if (!lossw) return -2;
     memset(out, 0, sizeof(double) * 2 * (size_t)nphi);
-    int rc = run(&p, nthreads, NULL, lossw, out);
+    int rc = run(&p, 0, nnode, nthreads, NULL, lossw, out);
     free(lossw);
     return rc;
 }

@@ -1,0 +1,187 @@
+"""ctypes binding of libpgboltz.so (the C ABI in include/pg_boltz.h).
+
+Argument marshalling only: every step of the collision operator runs in the
+library's CUDA kernels.  Device arrays are passed as raw pointers; callers may
+hand in torch CUDA tensors (float64, contiguous), whose data_ptr() is used.
+There is no CPU fallback: if the library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from functools import lru_cache
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libpgboltz.so")
+
+PG_OK, PG_ERR_ARG, PG_ERR_NOMEM, PG_ERR_CUDA, PG_ERR_TIMEOUT, PG_ERR_STATE = 0, -1, -2, -3, -4, -5
+PG_PREC_AUTO, PG_PREC_FP64, PG_PREC_FP32 = 0, 1, 2
+PG_SPHERE_AUTO, PG_SPHERE_ANTIPODAL, PG_SPHERE_FIBONACCI = 0, 1, 2
+
+# Every symbol the header declares (checked by the ABI test).
+EXPORTS = (
+    "pg_boltz_plan", "pg_boltz_plan_ex", "pg_boltz_set_stream", "pg_boltz_collide",
+    "pg_boltz_moments", "pg_boltz_project_nodes", "pg_boltz_project", "pg_boltz_info",
+    "pg_boltz_destroy", "pg_boltz_last_error", "pg_boltz_debug_fail_alloc", "pg_boltz_set_timing",
+    "pg_boltz_stage_times",
+)
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_int), ("N", ctypes.c_int), ("M", ctypes.c_int),
+        ("S", ctypes.c_double), ("kernel_gamma", ctypes.c_double), ("tol", ctypes.c_double),
+        ("map_log", ctypes.c_int), ("precision", ctypes.c_int), ("sphere", ctypes.c_int),
+        ("upsampfac", ctypes.c_double), ("proj_nodes", ctypes.c_int),
+        ("spread_threads", ctypes.c_int), ("spread_blocks_per_sm", ctypes.c_int),
+    ]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_int), ("N", ctypes.c_int), ("M", ctypes.c_int), ("r", ctypes.c_int),
+        ("precision", ctypes.c_int), ("sphere", ctypes.c_int),
+        ("S", ctypes.c_double), ("kernel_gamma", ctypes.c_double), ("tol", ctypes.c_double),
+        ("upsampfac", ctypes.c_double),
+        ("n_grid", ctypes.c_int), ("n_fold", ctypes.c_int), ("kernel_width", ctypes.c_int),
+        ("kernel_beta", ctypes.c_double), ("slabs", ctypes.c_int),
+        ("spread_blocks", ctypes.c_int), ("spread_threads", ctypes.c_int),
+        ("spread_smem_bytes", ctypes.c_size_t),
+        ("points", ctypes.c_longlong), ("pairs", ctypes.c_longlong),
+        ("proj_nodes", ctypes.c_int), ("launches_per_collide", ctypes.c_int),
+        ("device_bytes", ctypes.c_size_t),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class PGBoltzError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+@lru_cache(maxsize=1)
+def lib():
+    """Load libpgboltz.so; raises if it has not been built (no fallback exists)."""
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2105_08806_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    L.pg_boltz_plan.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double]
+    L.pg_boltz_plan.restype = vp
+    L.pg_boltz_plan_ex.argtypes = [ctypes.POINTER(Opts)]
+    L.pg_boltz_plan_ex.restype = vp
+    L.pg_boltz_set_stream.argtypes = [vp, vp]
+    L.pg_boltz_collide.argtypes = [vp, vp, vp]
+    L.pg_boltz_moments.argtypes = [vp, dp]
+    L.pg_boltz_project_nodes.argtypes = [vp, dp, ip]
+    L.pg_boltz_project.argtypes = [vp, vp, vp]
+    L.pg_boltz_info.argtypes = [vp, ctypes.POINTER(Info)]
+    L.pg_boltz_destroy.argtypes = [vp]
+    L.pg_boltz_destroy.restype = None
+    L.pg_boltz_last_error.restype = ctypes.c_char_p
+    L.pg_boltz_debug_fail_alloc.argtypes = [ctypes.c_int]
+    L.pg_boltz_debug_fail_alloc.restype = None
+    L.pg_boltz_set_timing.argtypes = [vp, ctypes.c_int]
+    L.pg_boltz_stage_times.argtypes = [vp, dp]
+    for name in ("pg_boltz_set_timing", "pg_boltz_stage_times", "pg_boltz_set_stream", "pg_boltz_collide", "pg_boltz_moments", "pg_boltz_project_nodes",
+                 "pg_boltz_project", "pg_boltz_info"):
+        getattr(L, name).restype = ctypes.c_int
+    return L
+
+
+def last_error() -> str:
+    return lib().pg_boltz_last_error().decode()
+
+
+def _check(code):
+    if code != PG_OK:
+        raise PGBoltzError(code, last_error())
+
+
+def _ptr(x):
+    """Raw device pointer of a torch tensor (float64, contiguous, CUDA) or an int."""
+    if isinstance(x, int):
+        return x
+    if not x.is_cuda or not x.is_contiguous() or str(x.dtype) != "torch.float64":
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return x.data_ptr()
+
+
+class Plan:
+    """One collision-operator plan (pg_boltz_plan_ex).  Use as a context manager or call close()."""
+
+    def __init__(self, d, N, M, S, kernel_gamma, tol, *, map_log=False, precision=PG_PREC_AUTO,
+                 sphere=PG_SPHERE_AUTO, upsampfac=0.0, proj_nodes=0, spread_threads=0,
+                 spread_blocks_per_sm=0):
+        o = Opts(d=d, N=N, M=M, S=S, kernel_gamma=kernel_gamma, tol=tol, map_log=int(map_log),
+                 precision=precision, sphere=sphere, upsampfac=upsampfac, proj_nodes=proj_nodes,
+                 spread_threads=spread_threads, spread_blocks_per_sm=spread_blocks_per_sm)
+        h = lib().pg_boltz_plan_ex(ctypes.byref(o))
+        if not h:
+            raise PGBoltzError(PG_ERR_ARG, last_error())
+        self._h = ctypes.c_void_p(h)
+        self.d, self.N, self.M = d, N, M
+        self.n_modes = (N + 1) ** d
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None for the default stream."""
+        raw = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+        _check(lib().pg_boltz_set_stream(self._h, ctypes.c_void_p(raw)))
+
+    def collide(self, f, Q):
+        _check(lib().pg_boltz_collide(self._h, ctypes.c_void_p(_ptr(f)), ctypes.c_void_p(_ptr(Q))))
+
+    def moments(self):
+        out = (ctypes.c_double * 6)()
+        _check(lib().pg_boltz_moments(self._h, out))
+        keys = ("mass", "energy", "mass_gain", "energy_gain", "norm_Q", "norm_gain")
+        return dict(zip(keys, list(out)))
+
+    def set_timing(self, enable: bool):
+        _check(lib().pg_boltz_set_timing(self._h, int(bool(enable))))
+
+    def stage_times(self):
+        """(reconstruct, loss, spread, transform) milliseconds of the last timed collide."""
+        out = (ctypes.c_double * 4)()
+        _check(lib().pg_boltz_stage_times(self._h, out))
+        return list(out)
+
+    def project_nodes(self):
+        cnt = ctypes.c_int(0)
+        _check(lib().pg_boltz_project_nodes(self._h, None, ctypes.byref(cnt)))
+        buf = (ctypes.c_double * cnt.value)()
+        _check(lib().pg_boltz_project_nodes(self._h, buf, ctypes.byref(cnt)))
+        return list(buf)
+
+    def project(self, fvals, ftilde):
+        _check(lib().pg_boltz_project(self._h, ctypes.c_void_p(_ptr(fvals)), ctypes.c_void_p(_ptr(ftilde))))
+
+    def info(self) -> dict:
+        inf = Info()
+        _check(lib().pg_boltz_info(self._h, ctypes.byref(inf)))
+        return inf.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().pg_boltz_destroy(self._h)
+        self._h = ctypes.c_void_p(0)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,67 @@
+// Internal declarations of the sm_103a collision-operator library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "pg_boltz.h"
+
+namespace pgb {
+
+// Everything the spreading kernel reads, passed by value.  The nodes, weights and
+// coefficients are in the kernel's arithmetic type T (float or double).
+struct SpreadArgs {
+    int d, N, M, r;
+    int nnode;            // N^d interior nodes
+    long long npairs;     // nnode^2 (i, j) pairs
+    int n, nf;            // periodic grid size, folded cells per axis (n/2 + 1)
+    int rows_per_slab;    // folded-grid rows (axis 0) held in shared memory by one block
+    int nslab;            // number of slabs covering axis 0
+    int fast_gamma;       // 0: gamma = 0, 1: gamma = 1, 2: gamma = 1/2, 3: general pow
+    double S, gamma, Bconst;
+    double beta;          // exponential-of-semicircle shape
+    double grid_scale;    // n / (2 pi): angle -> grid coordinate
+    const void *vnode;    // N node velocities (same on every axis)
+    const void *a;        // nnode values a_i = W_i g_i
+    const void *sig;      // M x d sphere points
+    const void *wsig;     // M sphere weights
+    double *grid;         // nf^d folded grid, FP64, accumulated with atomics
+};
+
+// Launch the spreading kernel for (T, d, w); returns cudaSuccess or the launch error.
+cudaError_t launch_spread_f32(const SpreadArgs &a, int w, int blocks, int threads, size_t smem,
+                              cudaStream_t s);
+cudaError_t launch_spread_f64(const SpreadArgs &a, int w, int blocks, int threads, size_t smem,
+                              cudaStream_t s);
+// Highest kernel width with a compiled spreading kernel for each type.
+constexpr int kMaxWidthF32 = 10;
+constexpr int kMaxWidthF64 = 16;
+constexpr int kMinWidth = 2;
+
+// Three-axis shape of a C-order array; 2D arrays use e0 = 1.
+struct Dims3 {
+    int e[3];
+};
+
+// out = A contracted with `in` along axis `ax` (A is m x in.e[ax], row-major).
+cudaError_t launch_axis_pass(const double *in, Dims3 in_dims, int ax, const double *A, int m,
+                             double *out, cudaStream_t s);
+// Last reconstruction pass along axis 2, then a_i = acc * prod_l scale[i_l];
+// writes a (FP64) and, if af != nullptr, a float copy.
+cudaError_t launch_recon_last(const double *in, Dims3 in_dims, const double *A, int m,
+                              const double *scale, int d, double *a, float *af, cudaStream_t s);
+// Loss: h_i = a_i * Lsum_i * prod_l inv_mu2[i_l], Lsum_i = Bw * sum_j a_j B(|v_i - v_j|).
+cudaError_t launch_loss(const double *a, const double *vnode, int N, int d, double gamma,
+                        int fast_gamma, double Bw, const double *inv_mu2, double *h,
+                        cudaStream_t s);
+// Final pass along axis 2: Qp = D . G, Qm = E . H, Q = Qp - Qm (also copied to Qcopy).
+cudaError_t launch_final(const double *G, Dims3 g_dims, const double *D, const double *H,
+                         Dims3 h_dims, const double *E, int m, double *Q, double *Qplus,
+                         double *Qcopy, cudaStream_t s);
+// Diagnostics: mass/energy functionals of Q and Qplus and their L2 norms into out[6].
+cudaError_t launch_moments(const double *Q, const double *Qplus, int d, int N, double S,
+                           double *out, cudaStream_t s);
+
+}  // namespace pgb

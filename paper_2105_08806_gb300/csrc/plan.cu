@@ -1,0 +1,712 @@
+// Host side of the collision-operator library: plan construction (quadrature
+// nodes, sphere sets, transform matrices, spreading-kernel parameters), the
+// C ABI entry points and the launch sequence of one evaluation.
+//
+// Quadrature (Section 4.1-4.2): M_v = N + 2 Chebyshev-Gauss-Lobatto nodes per
+// axis, xi_i = -cos(pi i/(N+1)), i = 0..N+1, weight pi/(N+1) (halved at the ends).
+// The end nodes map to v = -inf, +inf where f_N = mu^4 P vanishes, so only the N
+// interior nodes i = 1..N carry weight.  With phi_i = pi i/(N+1):
+//   T_k(xi_i) = cos(k (pi - phi_i)),  1 - xi_i^2 = sin^2 phi_i,
+//   mu(xi_i)^2 = sin(phi_i)^(1+r) / S                       (Eq. 1D_mu_function)
+//   v_i = -S cot(phi_i)            (r = 1, Eq. algebraic)
+//   v_i =  S ln tan(phi_i / 2)     (r = 0, Eq. logarithmic)
+// a_i = W_i g_i = prod_l (pi/(N+1)) mu(xi_{i_l})^2 P_i with P_i = sum_k f~_k T_k(xi_i)/sqrt(c_k).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pg_boltz.h"
+#include "pgb_internal.cuh"
+
+#define PG_API extern "C" __attribute__((visibility("default")))
+
+namespace {
+
+thread_local std::string g_last_error;
+std::atomic<int> g_fail_alloc_countdown{0};
+
+int set_error(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+const double kPi = 3.14159265358979323846;
+
+// Make `dev` current for the lifetime of the guard and restore the caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on P_n).
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
+{
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = -z;
+        x[n - 1 - i] = z;
+        w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+}  // namespace
+
+struct pg_boltz_plan_s {
+    pg_boltz_info_t info{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int d = 2, N = 2, M = 2, r = 1, prec = PG_PREC_FP64, Mp = 0;
+    double S = 1.0, gamma = 0.0, tol = 1e-6, sigma_up = 2.0;
+    int n = 0, nf = 0, w = 0;
+    double beta = 0.0;
+    int nnode = 0;
+    long long npairs = 0;
+    int fast_gamma = 0;
+    double Bconst = 0.0, Wsig = 0.0;
+    int nslab = 1, rows_per_slab = 0, spread_blocks = 0, spread_threads = 256;
+    size_t spread_smem = 0;
+    size_t device_bytes = 0;
+    std::vector<void *> allocs;
+    std::vector<double> proj_v;  // host copy of projection node velocities
+    bool have_q = false;
+    int last_launches = 0;
+    // optional per-stage timing: events recorded on the plan's stream around the stages
+    bool timing = false;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool ev_recorded = false;
+
+    // device tables
+    double *R = nullptr;       // N x (N+1): T_k(xi_i)/sqrt(c_k), interior nodes
+    double *E = nullptr;       // (N+1) x N: transpose of R
+    double *Dm = nullptr;      // (N+1) x nf: cosine transform + deconvolution
+    double *Pm = nullptr;      // (N+1) x Mp: projection
+    double *scale_a = nullptr; // N: (pi/(N+1)) mu_i^2
+    double *inv_mu2 = nullptr; // N: 1/mu_i^2
+    double *v64 = nullptr;     // N node velocities
+    float *v32 = nullptr;
+    double *sig64 = nullptr, *wsig64 = nullptr;  // M x d, M
+    float *sig32 = nullptr, *wsig32 = nullptr;
+    // workspace
+    double *tA = nullptr, *tB = nullptr, *tC = nullptr, *tD = nullptr;
+    double *a64 = nullptr;
+    float *a32 = nullptr;
+    double *h = nullptr, *grid = nullptr, *Qplus = nullptr, *Qlast = nullptr, *mom = nullptr;
+};
+
+namespace {
+
+int dev_alloc(pg_boltz_plan_t *p, void **ptr, size_t bytes)
+{
+    *ptr = nullptr;
+    int c = g_fail_alloc_countdown.load();
+    if (c > 0) {
+        if (g_fail_alloc_countdown.fetch_sub(1) == 1)
+            return set_error(PG_ERR_NOMEM, "device allocation of %zu bytes failed (injected)", bytes);
+    }
+    cudaError_t e = cudaMalloc(ptr, bytes < 16 ? 16 : bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return set_error(e == cudaErrorMemoryAllocation ? PG_ERR_NOMEM : PG_ERR_CUDA,
+                         "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    p->allocs.push_back(*ptr);
+    p->device_bytes += bytes;
+    return PG_OK;
+}
+
+template <typename T>
+int upload(pg_boltz_plan_t *p, T **dst, const std::vector<T> &src)
+{
+    int rc = dev_alloc(p, reinterpret_cast<void **>(dst), src.size() * sizeof(T));
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return set_error(PG_ERR_CUDA, "upload failed: %s", cudaGetErrorString(e));
+    return PG_OK;
+}
+
+void free_plan(pg_boltz_plan_t *p)
+{
+    if (!p) return;
+    for (cudaEvent_t &e : p->ev)
+        if (e) cudaEventDestroy(e);
+    for (void *q : p->allocs) cudaFree(q);
+    p->allocs.clear();
+    delete p;
+}
+
+double ipow(double x, int k)
+{
+    double r = 1.0;
+    for (int i = 0; i < k; ++i) r *= x;
+    return r;
+}
+
+// Kernel width for precision tol at oversampling sigma.  The exponential-of-semicircle
+// spreading error decays like exp(-pi w sqrt(1 - 1/sigma)); the constants are fitted to
+// measured errors of the folded cosine transform against direct sums (0.9 decades per
+// unit of w at sigma = 2, 0.8 decades offset).
+int width_for(double tol, double sigma)
+{
+    double per_w = 0.9 * std::sqrt(2.0 * (1.0 - 1.0 / sigma));
+    int w = (int)std::ceil((-std::log10(tol) - 0.8) / per_w);
+    return std::max(w, pgb::kMinWidth);
+}
+
+// psi_hat(k) = int psi(x) cos(k x) dx with psi(x) = exp(beta (sqrt(1 - (x/alpha)^2) - 1)),
+// |x| < alpha = w pi / n.  With x = alpha sin(theta) the integrand is smooth:
+// alpha int_{-pi/2}^{pi/2} exp(beta (cos theta - 1)) cos(k alpha sin theta) cos theta dtheta.
+std::vector<double> kernel_ft(int N, int w, double beta, int n)
+{
+    std::vector<double> gx, gw;
+    gauss_legendre(256, gx, gw);
+    const double alpha = w * kPi / n;
+    std::vector<double> out(N + 1);
+    for (int k = 0; k <= N; ++k) {
+        double acc = 0.0;
+        for (size_t t = 0; t < gx.size(); ++t) {
+            double th = 0.5 * kPi * gx[t];
+            acc += gw[t] * std::exp(beta * (std::cos(th) - 1.0)) * std::cos(k * alpha * std::sin(th)) *
+                   std::cos(th);
+        }
+        out[k] = alpha * 0.5 * kPi * acc;
+    }
+    return out;
+}
+
+void sphere_points(int d, int M, int kind, std::vector<double> &pts, std::vector<double> &wts)
+{
+    pts.assign((size_t)M * d, 0.0);
+    if (d == 2) {
+        for (int m = 0; m < M; ++m) {
+            double th = 2.0 * kPi * m / M;
+            pts[2 * m] = std::cos(th);
+            pts[2 * m + 1] = std::sin(th);
+        }
+        wts.assign(M, 2.0 * kPi / M);
+        return;
+    }
+    const double golden = kPi * (3.0 - std::sqrt(5.0));
+    if (kind == PG_SPHERE_FIBONACCI) {
+        for (int m = 0; m < M; ++m) {
+            double z = 1.0 - (2.0 * m + 1.0) / M;
+            double rho = std::sqrt(1.0 - z * z);
+            pts[3 * m] = rho * std::cos(m * golden);
+            pts[3 * m + 1] = rho * std::sin(m * golden);
+            pts[3 * m + 2] = z;
+        }
+    } else {
+        const int h = M / 2;
+        for (int m = 0; m < h; ++m) {
+            double z = 1.0 - (2.0 * m + 1.0) / h;
+            double rho = std::sqrt(1.0 - z * z);
+            double x = rho * std::cos(m * golden), y = rho * std::sin(m * golden);
+            pts[3 * m] = x;
+            pts[3 * m + 1] = y;
+            pts[3 * m + 2] = z;
+            pts[3 * (m + h)] = -x;
+            pts[3 * (m + h) + 1] = -y;
+            pts[3 * (m + h) + 2] = -z;
+        }
+    }
+    wts.assign(M, 4.0 * kPi / M);
+}
+
+double map_v(double phi, double S, int r)
+{
+    // xi = -cos(phi); r = 1: v = S xi / sqrt(1 - xi^2) = -S cot(phi); r = 0: v = S atanh(xi) = S ln tan(phi/2)
+    if (r == 1) return -S * std::cos(phi) / std::sin(phi);
+    return S * std::log(std::tan(0.5 * phi));
+}
+
+int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
+{
+    const int d = p->d, N = p->N, M = p->M;
+    p->nnode = (d == 2) ? N * N : N * N * N;
+    p->npairs = (long long)p->nnode * p->nnode;
+    p->fast_gamma = (p->gamma == 0.0) ? 0 : (p->gamma == 1.0) ? 1 : (p->gamma == 0.5) ? 2 : 3;
+    p->Bconst = 1.0 / (d == 2 ? 2.0 * kPi : 4.0 * kPi);
+
+    // ---- transform / spreading parameters
+    p->sigma_up = (o.upsampfac > 0.0) ? o.upsampfac : 2.0;
+    p->n = (int)std::ceil(p->sigma_up * (2 * N + 1));
+    if (p->n % 2) p->n += 1;
+    p->nf = p->n / 2 + 1;
+    p->w = width_for(p->tol, p->sigma_up);
+    const int wmax = (p->prec == PG_PREC_FP32) ? pgb::kMaxWidthF32 : pgb::kMaxWidthF64;
+    if (p->w > wmax) {
+        if (p->prec == PG_PREC_FP32) p->w = wmax;  // FP32 spreading cannot resolve more anyway
+        else return set_error(PG_ERR_ARG, "tol %g needs kernel width %d > %d", p->tol, p->w, wmax);
+    }
+    p->beta = 0.97 * kPi * (1.0 - 0.5 / p->sigma_up) * p->w;
+    p->Mp = (o.proj_nodes > 0) ? o.proj_nodes : 4 * (N + 1);
+
+    // ---- node tables
+    std::vector<double> R((size_t)N * (N + 1)), E((size_t)(N + 1) * N), sa(N), im(N), v(N);
+    std::vector<float> vf(N);
+    const double wnode = kPi / (N + 1);
+    for (int i = 0; i < N; ++i) {
+        const double phi = kPi * (i + 1) / (N + 1);
+        const double mu2 = ipow(std::sin(phi), 1 + p->r) / p->S;
+        sa[i] = wnode * mu2;
+        im[i] = 1.0 / mu2;
+        v[i] = map_v(phi, p->S, p->r);
+        vf[i] = (float)v[i];
+        for (int k = 0; k <= N; ++k) {
+            const double tk = std::cos(k * (kPi - phi)) / std::sqrt(k == 0 ? kPi : 0.5 * kPi);
+            R[(size_t)i * (N + 1) + k] = tk;
+            E[(size_t)k * N + i] = tk;
+        }
+    }
+    // ---- cosine transform with deconvolution: D[k][g] = (2 pi/n) cos(2 pi k g/n) / (sqrt(c_k) psi_hat(k))
+    std::vector<double> ph = kernel_ft(N, p->w, p->beta, p->n);
+    std::vector<double> D((size_t)(N + 1) * p->nf);
+    for (int k = 0; k <= N; ++k) {
+        const double ck = std::sqrt(k == 0 ? kPi : 0.5 * kPi);
+        for (int g = 0; g < p->nf; ++g) {
+            const long long kg = ((long long)k * g) % p->n;
+            D[(size_t)k * p->nf + g] = (2.0 * kPi / p->n) * std::cos(2.0 * kPi * (double)kg / p->n) / (ck * ph[k]);
+        }
+    }
+    // ---- projection (Chebyshev-Gauss): P[k][p] = (pi/Mp) mu_p^-4 T_k(xi_p) / sqrt(c_k)
+    const int Mp = p->Mp;
+    std::vector<double> P((size_t)(N + 1) * Mp);
+    p->proj_v.assign(Mp, 0.0);
+    for (int q = 0; q < Mp; ++q) {
+        const double phi = (2.0 * q + 1.0) * kPi / (2.0 * Mp);
+        const double mu_m4 = p->S * p->S / ipow(std::sin(phi), 2 * (1 + p->r));
+        p->proj_v[q] = map_v(phi, p->S, p->r);
+        for (int k = 0; k <= N; ++k)
+            P[(size_t)k * Mp + q] = (kPi / Mp) * mu_m4 * std::cos(k * (kPi - phi)) / std::sqrt(k == 0 ? kPi : 0.5 * kPi);
+    }
+    // ---- sphere set
+    std::vector<double> sp, sw;
+    sphere_points(d, M, p->info.sphere, sp, sw);
+    p->Wsig = 0.0;
+    for (double x : sw) p->Wsig += x;
+    std::vector<float> spf(sp.begin(), sp.end()), swf(sw.begin(), sw.end());
+
+    int rc;
+    if ((rc = upload(p, &p->R, R)) || (rc = upload(p, &p->E, E)) || (rc = upload(p, &p->Dm, D)) ||
+        (rc = upload(p, &p->Pm, P)) || (rc = upload(p, &p->scale_a, sa)) || (rc = upload(p, &p->inv_mu2, im)) ||
+        (rc = upload(p, &p->v64, v)) || (rc = upload(p, &p->v32, vf)) || (rc = upload(p, &p->sig64, sp)) ||
+        (rc = upload(p, &p->wsig64, sw)) || (rc = upload(p, &p->sig32, spf)) || (rc = upload(p, &p->wsig32, swf)))
+        return rc;
+
+    // ---- workspace
+    const long long modes = (long long)ipow(N + 1, d);
+    const long long nfd1 = (long long)ipow(p->nf, d - 1);
+    const long long mpd1 = (long long)ipow(Mp, d - 1);
+    const long long big = std::max({modes, (long long)(N + 1) * nfd1, (long long)(N + 1) * mpd1});
+    const long long grid_cells = nfd1 * p->nf;
+    if ((rc = dev_alloc(p, (void **)&p->tA, big * 8)) || (rc = dev_alloc(p, (void **)&p->tB, big * 8)) ||
+        (rc = dev_alloc(p, (void **)&p->tC, modes * 8)) || (rc = dev_alloc(p, (void **)&p->tD, modes * 8)) ||
+        (rc = dev_alloc(p, (void **)&p->a64, (size_t)p->nnode * 8)) ||
+        (rc = dev_alloc(p, (void **)&p->a32, (size_t)p->nnode * 4)) ||
+        (rc = dev_alloc(p, (void **)&p->h, (size_t)p->nnode * 8)) ||
+        (rc = dev_alloc(p, (void **)&p->grid, grid_cells * 8)) ||
+        (rc = dev_alloc(p, (void **)&p->Qplus, modes * 8)) || (rc = dev_alloc(p, (void **)&p->Qlast, modes * 8)) ||
+        (rc = dev_alloc(p, (void **)&p->mom, 8 * 8)))
+        return rc;
+
+    // ---- spreading launch shape
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, p->device);
+    if (e != cudaSuccess) return set_error(PG_ERR_CUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e));
+    const size_t elem = (p->prec == PG_PREC_FP32) ? 4 : 8;
+    const size_t plane = (size_t)nfd1;
+    const size_t max_smem = prop.sharedMemPerBlockOptin;
+    int rows_fit = (int)std::min<size_t>(p->nf, max_smem / (plane * elem));
+    if (rows_fit < 1) return set_error(PG_ERR_ARG, "folded grid plane of %zu cells does not fit shared memory", plane);
+    p->nslab = (p->nf + rows_fit - 1) / rows_fit;
+    p->rows_per_slab = (p->nf + p->nslab - 1) / p->nslab;
+    p->nslab = (p->nf + p->rows_per_slab - 1) / p->rows_per_slab;  // no empty trailing slab
+    p->spread_smem = (size_t)p->rows_per_slab * plane * elem;
+    p->spread_threads = (o.spread_threads > 0) ? o.spread_threads : 256;
+    if (p->spread_threads % 32 || p->spread_threads > 256)
+        return set_error(PG_ERR_ARG, "spread_threads must be a multiple of 32 and <= 256");
+    int per_sm = (int)(prop.sharedMemPerMultiprocessor / (p->spread_smem + prop.reservedSharedMemPerBlock));
+    per_sm = std::min(per_sm, prop.maxThreadsPerMultiProcessor / p->spread_threads);
+    if (o.spread_blocks_per_sm > 0) per_sm = std::min(per_sm, o.spread_blocks_per_sm);
+    per_sm = std::max(per_sm, 1);
+    long long blocks = (long long)prop.multiProcessorCount * per_sm;
+    blocks = std::max<long long>(blocks / p->nslab, 1) * p->nslab;
+    const long long need = ((p->npairs + p->spread_threads - 1) / p->spread_threads) * p->nslab;
+    blocks = std::min(blocks, need);
+    p->spread_blocks = (int)blocks;
+    return PG_OK;
+}
+
+int validate(const pg_boltz_opts_t &o)
+{
+    if (o.d != 2 && o.d != 3) return set_error(PG_ERR_ARG, "d must be 2 or 3 (got %d)", o.d);
+    if (o.N < 2 || o.N > (o.d == 2 ? 512 : 128)) return set_error(PG_ERR_ARG, "N out of range (got %d)", o.N);
+    if (o.M < 2 || (o.M % 2)) return set_error(PG_ERR_ARG, "M must be even and >= 2 (got %d)", o.M);
+    if (!(o.S > 0.0) || !std::isfinite(o.S)) return set_error(PG_ERR_ARG, "S must be positive (got %g)", o.S);
+    if (!(o.kernel_gamma >= 0.0 && o.kernel_gamma <= 1.0))
+        return set_error(PG_ERR_ARG, "kernel_gamma must be in [0, 1] (got %g)", o.kernel_gamma);
+    if (!(o.tol >= 1e-15 && o.tol <= 1e-2)) return set_error(PG_ERR_ARG, "tol must be in [1e-15, 1e-2] (got %g)", o.tol);
+    if (o.map_log != 0 && o.map_log != 1) return set_error(PG_ERR_ARG, "map_log must be 0 or 1");
+    if (o.precision < PG_PREC_AUTO || o.precision > PG_PREC_FP32) return set_error(PG_ERR_ARG, "bad precision");
+    if (o.sphere < PG_SPHERE_AUTO || o.sphere > PG_SPHERE_FIBONACCI) return set_error(PG_ERR_ARG, "bad sphere kind");
+    if (o.upsampfac != 0.0 && !(o.upsampfac >= 1.5 && o.upsampfac <= 4.0))
+        return set_error(PG_ERR_ARG, "upsampfac must be in [1.5, 4] (got %g)", o.upsampfac);
+    if (o.proj_nodes < 0 || o.proj_nodes > 4096) return set_error(PG_ERR_ARG, "proj_nodes out of range");
+    return PG_OK;
+}
+
+pgb::Dims3 dims_of(int d, int a, int b, int c)
+{
+    pgb::Dims3 x;
+    if (d == 2) {
+        x.e[0] = 1;
+        x.e[1] = b;
+        x.e[2] = c;
+    } else {
+        x.e[0] = a;
+        x.e[1] = b;
+        x.e[2] = c;
+    }
+    return x;
+}
+
+int cuda_check(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return PG_OK;
+    return set_error(PG_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Contract every axis but the last of `in` (shape `dims`, the last d axes live) with A,
+// alternating between t1 and t2; returns the buffer holding the result and updates dims.
+int leading_passes(pg_boltz_plan_t *p, const double *in, pgb::Dims3 &dims, const double *A, int m,
+                   double *t1, double *t2, const double **out, int *launches)
+{
+    const double *cur = in;
+    double *bufs[2] = {t1, t2};
+    int which = 0;
+    for (int ax = 3 - p->d; ax < 2; ++ax) {
+        int rc = cuda_check(pgb::launch_axis_pass(cur, dims, ax, A, m, bufs[which], p->stream), "axis pass");
+        if (rc) return rc;
+        ++*launches;
+        dims.e[ax] = m;
+        cur = bufs[which];
+        which ^= 1;
+    }
+    *out = cur;
+    return PG_OK;
+}
+
+}  // namespace
+
+// ============================================================================ ABI
+
+PG_API const char *pg_boltz_last_error(void) { return g_last_error.c_str(); }
+
+PG_API void pg_boltz_debug_fail_alloc(int countdown) { g_fail_alloc_countdown.store(countdown > 0 ? countdown : 0); }
+
+PG_API pg_boltz_plan_t *pg_boltz_plan_ex(const pg_boltz_opts_t *opts)
+{
+    g_last_error.clear();
+    if (!opts) {
+        set_error(PG_ERR_ARG, "opts is NULL");
+        return nullptr;
+    }
+    pg_boltz_opts_t o = *opts;
+    if (validate(o)) return nullptr;
+    pg_boltz_plan_t *p = new (std::nothrow) pg_boltz_plan_t();
+    if (!p) {
+        set_error(PG_ERR_NOMEM, "host allocation failed");
+        return nullptr;
+    }
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        cudaGetLastError();
+        set_error(PG_ERR_CUDA, "no CUDA device available");
+        delete p;
+        return nullptr;
+    }
+    p->d = o.d;
+    p->N = o.N;
+    p->M = o.M;
+    p->S = o.S;
+    p->gamma = o.kernel_gamma;
+    p->tol = o.tol;
+    p->r = o.map_log ? 0 : 1;
+    p->prec = (o.precision == PG_PREC_AUTO) ? (o.tol < 1e-8 ? PG_PREC_FP64 : PG_PREC_FP32) : o.precision;
+    p->info.sphere = (o.d == 3) ? (o.sphere == PG_SPHERE_AUTO ? PG_SPHERE_ANTIPODAL : o.sphere) : PG_SPHERE_AUTO;
+    if (build_plan(p, o)) {
+        free_plan(p);
+        return nullptr;
+    }
+    pg_boltz_info_t &in = p->info;
+    in.d = p->d;
+    in.N = p->N;
+    in.M = p->M;
+    in.r = p->r;
+    in.precision = p->prec;
+    in.S = p->S;
+    in.kernel_gamma = p->gamma;
+    in.tol = p->tol;
+    in.upsampfac = p->sigma_up;
+    in.n_grid = p->n;
+    in.n_fold = p->nf;
+    in.kernel_width = p->w;
+    in.kernel_beta = p->beta;
+    in.slabs = p->nslab;
+    in.spread_blocks = p->spread_blocks;
+    in.spread_threads = p->spread_threads;
+    in.spread_smem_bytes = p->spread_smem;
+    in.pairs = p->npairs;
+    in.points = p->npairs * p->M;
+    in.proj_nodes = p->Mp;
+    in.launches_per_collide = 5 + 3 * (p->d - 1);
+    in.device_bytes = p->device_bytes;
+    return p;
+}
+
+PG_API pg_boltz_plan_t *pg_boltz_plan(int d, int N, int M, double S, double kernel_gamma, double tol)
+{
+    pg_boltz_opts_t o;
+    std::memset(&o, 0, sizeof(o));
+    o.d = d;
+    o.N = N;
+    o.M = M;
+    o.S = S;
+    o.kernel_gamma = kernel_gamma;
+    o.tol = tol;
+    return pg_boltz_plan_ex(&o);
+}
+
+PG_API int pg_boltz_set_stream(pg_boltz_plan_t *plan, void *cuda_stream)
+{
+    if (!plan) return set_error(PG_ERR_ARG, "plan is NULL");
+    plan->stream = static_cast<cudaStream_t>(cuda_stream);
+    return PG_OK;
+}
+
+PG_API int pg_boltz_collide(pg_boltz_plan_t *p, const double *f_dev, double *Q_dev)
+{
+    if (!p) return set_error(PG_ERR_ARG, "plan is NULL");
+    if (!f_dev || !Q_dev) return set_error(PG_ERR_ARG, "f or Q is NULL");
+    const long long modes = (long long)ipow(p->N + 1, p->d);
+    const char *fb = reinterpret_cast<const char *>(f_dev);
+    const char *qb = reinterpret_cast<const char *>(Q_dev);
+    if (fb < qb + modes * 8 && qb < fb + modes * 8) return set_error(PG_ERR_ARG, "f and Q overlap");
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return set_error(PG_ERR_CUDA, "cannot select the plan's device");
+    const int d = p->d, N = p->N;
+    int launches = 0, rc;
+    const bool f32 = (p->prec == PG_PREC_FP32);
+
+    auto mark = [&](int k) {
+        if (p->timing) cudaEventRecord(p->ev[k], p->stream);
+    };
+    mark(0);
+    // 1. reconstruct a_i = W_i mu_i^2 sum_k f~_k T_k(xi_i)/sqrt(c_k)   (Section 4.2)
+    pgb::Dims3 dims = dims_of(d, N + 1, N + 1, N + 1);
+    const double *cur = nullptr;
+    if ((rc = leading_passes(p, f_dev, dims, p->R, N, p->tA, p->tB, &cur, &launches))) return rc;
+    if ((rc = cuda_check(pgb::launch_recon_last(cur, dims, p->R, N, p->scale_a, d, p->a64, f32 ? p->a32 : nullptr,
+                                                p->stream), "reconstruct")))
+        return rc;
+    ++launches;
+    mark(1);
+    // 2. loss weights h_i = a_i L_i / mu_i^2   (Eq. Qminus, inner sum over v_*, sigma)
+    if ((rc = cuda_check(pgb::launch_loss(p->a64, p->v64, N, d, p->gamma, p->fast_gamma, p->Bconst * p->Wsig,
+                                          p->inv_mu2, p->h, p->stream), "loss")))
+        return rc;
+    ++launches;
+    mark(2);
+    // 3. spread the M N^(2d) post-collision points onto the folded grid   (Eq. num_fast_k, Eq. nufft)
+    const size_t grid_bytes = (size_t)ipow(p->nf, d) * 8;
+    if ((rc = cuda_check(cudaMemsetAsync(p->grid, 0, grid_bytes, p->stream), "memset grid"))) return rc;
+    ++launches;
+    pgb::SpreadArgs sa;
+    sa.d = d;
+    sa.N = N;
+    sa.M = p->M;
+    sa.r = p->r;
+    sa.nnode = p->nnode;
+    sa.npairs = p->npairs;
+    sa.n = p->n;
+    sa.nf = p->nf;
+    sa.rows_per_slab = p->rows_per_slab;
+    sa.nslab = p->nslab;
+    sa.fast_gamma = p->fast_gamma;
+    sa.S = p->S;
+    sa.gamma = p->gamma;
+    sa.Bconst = p->Bconst;
+    sa.beta = p->beta;
+    sa.grid_scale = p->n / (2.0 * kPi);
+    sa.vnode = f32 ? (const void *)p->v32 : (const void *)p->v64;
+    sa.a = f32 ? (const void *)p->a32 : (const void *)p->a64;
+    sa.sig = f32 ? (const void *)p->sig32 : (const void *)p->sig64;
+    sa.wsig = f32 ? (const void *)p->wsig32 : (const void *)p->wsig64;
+    sa.grid = p->grid;
+    cudaError_t e = f32 ? pgb::launch_spread_f32(sa, p->w, p->spread_blocks, p->spread_threads, p->spread_smem, p->stream)
+                        : pgb::launch_spread_f64(sa, p->w, p->spread_blocks, p->spread_threads, p->spread_smem, p->stream);
+    if ((rc = cuda_check(e, "spread"))) return rc;
+    ++launches;
+    mark(3);
+    // 4. cosine transform + deconvolution of the grid, forward Chebyshev transform of the loss
+    pgb::Dims3 gd = dims_of(d, p->nf, p->nf, p->nf);
+    const double *gcur = nullptr;
+    if ((rc = leading_passes(p, p->grid, gd, p->Dm, N + 1, p->tA, p->tB, &gcur, &launches))) return rc;
+    pgb::Dims3 hd = dims_of(d, N, N, N);
+    const double *hcur = nullptr;
+    if ((rc = leading_passes(p, p->h, hd, p->E, N + 1, p->tC, p->tD, &hcur, &launches))) return rc;
+    // 5. Q = Q+ - Q-
+    if ((rc = cuda_check(pgb::launch_final(gcur, gd, p->Dm, hcur, hd, p->E, N + 1, Q_dev, p->Qplus, p->Qlast, p->stream),
+                         "final")))
+        return rc;
+    ++launches;
+    mark(4);
+    p->ev_recorded = p->timing;
+    p->last_launches = launches;
+    p->info.launches_per_collide = launches;
+    p->have_q = true;
+    return PG_OK;
+}
+
+PG_API int pg_boltz_moments(pg_boltz_plan_t *p, double *out_host)
+{
+    if (!p || !out_host) return set_error(PG_ERR_ARG, "NULL argument");
+    if (!p->have_q) return set_error(PG_ERR_STATE, "no pg_boltz_collide has run on this plan");
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return set_error(PG_ERR_CUDA, "cannot select the plan's device");
+    int rc;
+    if ((rc = cuda_check(pgb::launch_moments(p->Qlast, p->Qplus, p->d, p->N, p->S, p->mom, p->stream), "moments")))
+        return rc;
+    double tmp[6];
+    if ((rc = cuda_check(cudaMemcpyAsync(tmp, p->mom, sizeof(tmp), cudaMemcpyDeviceToHost, p->stream), "moments copy")))
+        return rc;
+    if ((rc = cuda_check(cudaStreamSynchronize(p->stream), "moments sync"))) return rc;
+    std::memcpy(out_host, tmp, sizeof(tmp));
+    return PG_OK;
+}
+
+PG_API int pg_boltz_set_timing(pg_boltz_plan_t *p, int enable)
+{
+    if (!p) return set_error(PG_ERR_ARG, "plan is NULL");
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return set_error(PG_ERR_CUDA, "cannot select the plan's device");
+    if (enable && !p->ev[0]) {
+        for (cudaEvent_t &e : p->ev) {
+            int rc = cuda_check(cudaEventCreate(&e), "cudaEventCreate");
+            if (rc) return rc;
+        }
+    }
+    p->timing = enable != 0;
+    p->ev_recorded = false;
+    return PG_OK;
+}
+
+PG_API int pg_boltz_stage_times(pg_boltz_plan_t *p, double *ms_out)
+{
+    if (!p || !ms_out) return set_error(PG_ERR_ARG, "NULL argument");
+    if (!p->ev_recorded) return set_error(PG_ERR_STATE, "no timed pg_boltz_collide since timing was enabled");
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return set_error(PG_ERR_CUDA, "cannot select the plan's device");
+    int rc = cuda_check(cudaEventSynchronize(p->ev[4]), "cudaEventSynchronize");
+    if (rc) return rc;
+    for (int k = 0; k < 4; ++k) {
+        float ms = 0.0f;
+        if ((rc = cuda_check(cudaEventElapsedTime(&ms, p->ev[k], p->ev[k + 1]), "cudaEventElapsedTime"))) return rc;
+        ms_out[k] = ms;
+    }
+    return PG_OK;
+}
+
+PG_API int pg_boltz_project_nodes(const pg_boltz_plan_t *p, double *v_host, int *count_out)
+{
+    if (!p) return set_error(PG_ERR_ARG, "plan is NULL");
+    if (count_out) *count_out = p->Mp;
+    if (v_host) std::memcpy(v_host, p->proj_v.data(), sizeof(double) * p->Mp);
+    return PG_OK;
+}
+
+PG_API int pg_boltz_project(pg_boltz_plan_t *p, const double *fvals_dev, double *ftilde_dev)
+{
+    if (!p) return set_error(PG_ERR_ARG, "plan is NULL");
+    if (!fvals_dev || !ftilde_dev) return set_error(PG_ERR_ARG, "NULL device pointer");
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return set_error(PG_ERR_CUDA, "cannot select the plan's device");
+    const int d = p->d, N = p->N, Mp = p->Mp;
+    pgb::Dims3 dims = dims_of(d, Mp, Mp, Mp);
+    const double *cur = fvals_dev;
+    double *bufs[2] = {p->tA, p->tB};
+    int which = 0;
+    for (int ax = 3 - d; ax < 3; ++ax) {
+        double *dst = (ax == 2) ? ftilde_dev : bufs[which];
+        int rc = cuda_check(pgb::launch_axis_pass(cur, dims, ax, p->Pm, N + 1, dst, p->stream), "projection pass");
+        if (rc) return rc;
+        dims.e[ax] = N + 1;
+        cur = dst;
+        which ^= 1;
+    }
+    return PG_OK;
+}
+
+PG_API int pg_boltz_info(const pg_boltz_plan_t *p, pg_boltz_info_t *out)
+{
+    if (!p || !out) return set_error(PG_ERR_ARG, "NULL argument");
+    *out = p->info;
+    out->device_bytes = p->device_bytes;
+    return PG_OK;
+}
+
+PG_API void pg_boltz_destroy(pg_boltz_plan_t *p)
+{
+    if (!p) return;
+    DeviceGuard guard(p->device);
+    cudaStreamSynchronize(p->stream);
+    free_plan(p);
+}

@@ -1,0 +1,264 @@
+// Small FP64 kernels around the spreading step:
+//  - separable axis passes (reconstruction of f_N at the nodes, Section 4.2; the
+//    cosine transform of the folded grid with the deconvolution folded into its
+//    matrix, Eq. nufft; the forward Chebyshev transform of the loss, Eq. Qminus;
+//    the projection of Eq. MultiD_spectral_coef),
+//  - the loss sum over node pairs (Eq. Qminus, inner integral),
+//  - the final pass that forms Q = Q+ - Q- (Section 4.2),
+//  - mass / energy diagnostics from the identities of Section 3.3.
+// All arrays are C-order three-axis arrays (2D arrays carry a leading axis of 1).
+#include <cuda_runtime.h>
+
+#include "pgb_internal.cuh"
+
+namespace pgb {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ long long stride_of(const Dims3 &d, int ax)
+{
+    return ax == 2 ? 1LL : (ax == 1 ? (long long)d.e[2] : (long long)d.e[1] * d.e[2]);
+}
+
+__global__ void k_axis_pass(const double *__restrict__ in, Dims3 id, int ax,
+                            const double *__restrict__ A, int m, double *__restrict__ out)
+{
+    Dims3 od = id;
+    od.e[ax] = m;
+    const long long total = (long long)od.e[0] * od.e[1] * od.e[2];
+    const int len = id.e[ax];
+    const long long sax = stride_of(id, ax);
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < total;
+         o += (long long)gridDim.x * blockDim.x) {
+        int oc[3];
+        oc[2] = (int)(o % od.e[2]);
+        const long long t = o / od.e[2];
+        oc[1] = (int)(t % od.e[1]);
+        oc[0] = (int)(t / od.e[1]);
+        const int k = oc[ax];
+        oc[ax] = 0;
+        const long long base = ((long long)oc[0] * id.e[1] + oc[1]) * id.e[2] + oc[2];
+        const double *arow = A + (long long)k * len;
+        double acc = 0.0;
+        for (int s = 0; s < len; ++s) acc = fma(arow[s], in[base + s * sax], acc);
+        out[o] = acc;
+    }
+}
+
+__global__ void k_recon_last(const double *__restrict__ in, Dims3 id, const double *__restrict__ A,
+                             int m, const double *__restrict__ scale, int d, double *__restrict__ a,
+                             float *__restrict__ af)
+{
+    const long long total = (long long)id.e[0] * id.e[1] * m;
+    const int len = id.e[2];
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < total;
+         o += (long long)gridDim.x * blockDim.x) {
+        const int o2 = (int)(o % m);
+        const long long t = o / m;
+        const int o1 = (int)(t % id.e[1]);
+        const int o0 = (int)(t / id.e[1]);
+        const double *src = in + ((long long)o0 * id.e[1] + o1) * len;
+        const double *arow = A + (long long)o2 * len;
+        double acc = 0.0;
+        for (int s = 0; s < len; ++s) acc = fma(arow[s], src[s], acc);
+        double sc = scale[o1] * scale[o2];
+        if (d == 3) sc *= scale[o0];
+        acc *= sc;
+        a[o] = acc;
+        if (af) af[o] = (float)acc;
+    }
+}
+
+template <int BLOCK>
+__device__ double block_sum(double v)
+{
+    __shared__ double warp_part[BLOCK / 32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) warp_part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < BLOCK / 32) ? warp_part[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    }
+    __syncthreads();
+    return s;  // valid in thread 0
+}
+
+constexpr int kLossThreads = 128;
+
+// One block per outer node i:  Lsum_i = Bw sum_j a_j |v_i - v_j|^gamma, h_i = a_i Lsum_i / mu_i^2.
+__global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict__ a,
+                                                        const double *__restrict__ vnode, int N,
+                                                        int d, double gamma, int fast_gamma,
+                                                        double Bw, const double *__restrict__ inv_mu2,
+                                                        double *__restrict__ h)
+{
+    const int nnode = (d == 2) ? N * N : N * N * N;
+    const int i = blockIdx.x;
+    int idx[3] = {0, 0, 0};
+    {
+        int t = i;
+        for (int l = d - 1; l >= 0; --l) {
+            idx[l] = t % N;
+            t /= N;
+        }
+    }
+    double vi[3];
+    for (int l = 0; l < 3; ++l) vi[l] = (l < d) ? vnode[idx[l]] : 0.0;
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < nnode; j += blockDim.x) {
+        int t = j;
+        double g2 = 0.0;
+        for (int l = d - 1; l >= 0; --l) {
+            const double dl = vi[l] - vnode[t % N];
+            t /= N;
+            g2 += dl * dl;
+        }
+        double B;
+        switch (fast_gamma) {
+        case 0: B = 1.0; break;
+        case 1: B = sqrt(g2); break;
+        case 2: B = sqrt(sqrt(g2)); break;
+        default: B = (g2 > 0.0) ? pow(g2, 0.5 * gamma) : 0.0; break;
+        }
+        acc = fma(a[j], B, acc);
+    }
+    const double tot = block_sum<kLossThreads>(acc);
+    if (threadIdx.x == 0) {
+        double sc = 1.0;
+        for (int l = 0; l < d; ++l) sc *= inv_mu2[idx[l]];
+        h[i] = a[i] * Bw * tot * sc;
+    }
+}
+
+__global__ void k_final(const double *__restrict__ G, Dims3 gd, const double *__restrict__ D,
+                        const double *__restrict__ H, Dims3 hd, const double *__restrict__ E, int m,
+                        double *__restrict__ Q, double *__restrict__ Qplus, double *__restrict__ Qcopy)
+{
+    const long long total = (long long)gd.e[0] * gd.e[1] * m;
+    const int lg = gd.e[2];
+    const int lh = hd.e[2];
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < total;
+         o += (long long)gridDim.x * blockDim.x) {
+        const int o2 = (int)(o % m);
+        const long long row = o / m;
+        const double *gsrc = G + row * lg;
+        const double *hsrc = H + row * lh;
+        const double *drow = D + (long long)o2 * lg;
+        const double *erow = E + (long long)o2 * lh;
+        double qp = 0.0, qm = 0.0;
+        for (int s = 0; s < lg; ++s) qp = fma(drow[s], gsrc[s], qp);
+        for (int s = 0; s < lh; ++s) qm = fma(erow[s], hsrc[s], qm);
+        Qplus[o] = qp;
+        Q[o] = qp - qm;
+        Qcopy[o] = qp - qm;
+    }
+}
+
+// 1 = a0 That_0 + a2 That_2 and v^2 = b0 That_0 + b2 That_2 per axis (Section 3.3 proof,
+// algebraic map): a0 = sqrt(c0)/(2S), a2 = -sqrt(c2)/(2S), b0 = sqrt(c0) S/2, b2 = sqrt(c2) S/2.
+__global__ void k_moments(const double *__restrict__ Q, const double *__restrict__ Qp, int d, int N,
+                          double S, double *__restrict__ out)
+{
+    const int nm = (d == 2) ? (N + 1) * (N + 1) : (N + 1) * (N + 1) * (N + 1);
+    double q2 = 0.0, p2 = 0.0;
+    for (int k = threadIdx.x; k < nm; k += blockDim.x) {
+        q2 += Q[k] * Q[k];
+        p2 += Qp[k] * Qp[k];
+    }
+    const double sq2 = block_sum<kThreads>(q2);
+    const double sp2 = block_sum<kThreads>(p2);
+    if (threadIdx.x == 0) {
+        const double pi = 3.14159265358979323846;
+        const double one[2] = {sqrt(pi) / (2.0 * S), -sqrt(pi / 2.0) / (2.0 * S)};
+        const double vsq[2] = {sqrt(pi) * S / 2.0, sqrt(pi / 2.0) * S / 2.0};
+        double mq = 0.0, eq = 0.0, mp = 0.0, ep = 0.0;
+        const int ncorner = 1 << d;
+        for (int c = 0; c < ncorner && N >= 2; ++c) {
+            int idx = 0;
+            double mass = 1.0, energy = 0.0;
+            for (int l = 0; l < d; ++l) {
+                const int bit = (c >> (d - 1 - l)) & 1;
+                idx = idx * (N + 1) + 2 * bit;
+                mass *= one[bit];
+            }
+            for (int l = 0; l < d; ++l) {
+                double term = 1.0;
+                for (int m2 = 0; m2 < d; ++m2) {
+                    const int bit = (c >> (d - 1 - m2)) & 1;
+                    term *= (m2 == l) ? vsq[bit] : one[bit];
+                }
+                energy += term;
+            }
+            mq += mass * Q[idx];
+            eq += energy * Q[idx];
+            mp += mass * Qp[idx];
+            ep += energy * Qp[idx];
+        }
+        out[0] = mq;
+        out[1] = eq;
+        out[2] = mp;
+        out[3] = ep;
+        out[4] = sqrt(sq2);
+        out[5] = sqrt(sp2);
+    }
+}
+
+int grid_for(long long total)
+{
+    long long b = (total + kThreads - 1) / kThreads;
+    if (b < 1) b = 1;
+    if (b > 4096) b = 4096;
+    return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_axis_pass(const double *in, Dims3 in_dims, int ax, const double *A, int m,
+                             double *out, cudaStream_t s)
+{
+    Dims3 od = in_dims;
+    od.e[ax] = m;
+    k_axis_pass<<<grid_for((long long)od.e[0] * od.e[1] * od.e[2]), kThreads, 0, s>>>(in, in_dims, ax,
+                                                                                     A, m, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_recon_last(const double *in, Dims3 in_dims, const double *A, int m,
+                              const double *scale, int d, double *a, float *af, cudaStream_t s)
+{
+    k_recon_last<<<grid_for((long long)in_dims.e[0] * in_dims.e[1] * m), kThreads, 0, s>>>(
+        in, in_dims, A, m, scale, d, a, af);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loss(const double *a, const double *vnode, int N, int d, double gamma,
+                        int fast_gamma, double Bw, const double *inv_mu2, double *h, cudaStream_t s)
+{
+    const int nnode = (d == 2) ? N * N : N * N * N;
+    k_loss<<<nnode, kLossThreads, 0, s>>>(a, vnode, N, d, gamma, fast_gamma, Bw, inv_mu2, h);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_final(const double *G, Dims3 g_dims, const double *D, const double *H,
+                         Dims3 h_dims, const double *E, int m, double *Q, double *Qplus,
+                         double *Qcopy, cudaStream_t s)
+{
+    k_final<<<grid_for((long long)g_dims.e[0] * g_dims.e[1] * m), kThreads, 0, s>>>(G, g_dims, D, H,
+                                                                                   h_dims, E, m, Q,
+                                                                                   Qplus, Qcopy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const double *Q, const double *Qplus, int d, int N, double S,
+                           double *out, cudaStream_t s)
+{
+    k_moments<<<1, kThreads, 0, s>>>(Q, Qplus, d, N, S, out);
+    return cudaGetLastError();
+}
+
+}  // namespace pgb

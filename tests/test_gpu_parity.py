@@ -1,0 +1,175 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
+
+Tolerances (relative L2 over the compared modes):
+  FP64 spreading path, tol = 1e-13:  1e-10
+  FP32 spreading path, tol = 1e-6:   1e-5
+Mode-level mass and energy (r = 1) are compared with the same functionals of the
+gain term: 1e-12 (FP64 path) and 1e-6 (FP32 path).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2105_08806_gb300 import PG_PREC_FP32, PG_PREC_FP64, PG_SPHERE_FIBONACCI
+from paper_2105_08806_gb300 import workloads as W
+
+from _helpers import flat_index, gpu_collide, rel_l2, sample_modes
+
+pytestmark = pytest.mark.gpu
+
+TOL64, TOL32 = 1e-10, 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    from paper_2105_08806_gb300.build import build
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build()
+    O.build()
+
+
+def _maxwell3(d, seed=0):
+    rng = np.random.default_rng(seed)
+    comps = [(1 / 3, rng.uniform(-1, 1, d), rng.uniform(0.6, 1.4)) for _ in range(3)]
+    return lambda p: sum(W.maxwellian(p, r, c, t) for r, c, t in comps)
+
+
+CASES = [
+    # d, N, M, S, gamma, map_log, sphere
+    (2, 16, 8, 2.0, 0.0, False, 0),    # 2D Maxwell molecules, N = 16, M = 8 (first workload)
+    (2, 24, 16, 3.0, 1.0, False, 0),   # hard spheres
+    (2, 12, 12, 2.5, 0.5, True, 0),    # logarithmic map, gamma = 1/2
+    (2, 7, 6, 1.5, 1.0, False, 0),     # odd N, M not divisible by 4
+    (2, 2, 2, 1.0, 0.0, False, 0),     # smallest plan: N = 2, M = 2
+    (3, 6, 16, 2.0, 0.5, False, 0),    # 3D, antipodal Fibonacci
+    (3, 5, 10, 2.0, 0.0, True, 0),     # 3D, logarithmic map
+    (3, 4, 8, 2.0, 1.0, False, PG_SPHERE_FIBONACCI),
+]
+
+
+@pytest.mark.parametrize("prec", [PG_PREC_FP64, PG_PREC_FP32])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"d{c[0]}N{c[1]}M{c[2]}g{c[4]}{'log' if c[5] else 'alg'}s{c[6]}")
+def test_all_modes_match_oracle(case, prec):
+    d, N, M, S, gamma, map_log, sphere = case
+    r = 0 if map_log else 1
+    fun = W.c1_2d_maxwell() if (d == 2 and N == 16) else _maxwell3(d, seed=N)
+    ft = O.project(fun, d, N, S, r).ravel()
+    gain, loss = O.collide_parts(ft, d, N, M, S, gamma, r=r,
+                                 sphere="fibonacci" if sphere == PG_SPHERE_FIBONACCI else "auto")
+    Qref = gain - loss
+    tol = 1e-13 if prec == PG_PREC_FP64 else 1e-6
+    Q, info, mom = gpu_collide(ft, d, N, M, S, gamma, tol, map_log=map_log, precision=prec, sphere=sphere)
+    err = rel_l2(Q, Qref)
+    assert err < (TOL64 if prec == PG_PREC_FP64 else TOL32), (err, info)
+    # gain term parity through the moments' norm of Q+
+    assert abs(mom["norm_gain"] - np.linalg.norm(gain)) <= (1e-10 if prec == PG_PREC_FP64 else 1e-5) * np.linalg.norm(gain)
+    if r == 1 and N >= 2:
+        ma, en = O.mass_energy_coeffs(d, N, S)
+        bound = 1e-12 if prec == PG_PREC_FP64 else 1e-6
+        assert abs(mom["mass"]) <= bound * abs(ma @ gain) + 1e-300
+        assert abs(mom["energy"]) <= bound * np.abs(en * gain).sum()
+
+
+def test_slabbed_3d_grid_fp64():
+    """3D N = 16 FP64: the folded grid (34^3 doubles) exceeds shared memory, so the spreading
+    runs in two slabs; sampled modes against the oracle."""
+    d, N, M, S, gamma = 3, 16, 8, 2.0, 0.0
+    ft = O.project(W.c3_3d_bkw(), d, N, S, 1).ravel()
+    modes = sample_modes(d, N, 40, seed=7)
+    gain, loss = O.collide_parts(ft, d, N, M, S, gamma, r=1, modes=modes)
+    Q, info, _ = gpu_collide(ft, d, N, M, S, gamma, 1e-13, precision=PG_PREC_FP64)
+    assert info["slabs"] >= 2
+    assert rel_l2(Q[flat_index(modes, N)], gain - loss) < TOL64
+
+
+def test_full_size_2d_hard_spheres_fp32_sampled_modes():
+    """The 2D hard-sphere workload at full size (N = 64, M = 32, S = 3) in the FP32 spreading
+    path, compared on a seeded mode subset the oracle computes one by one."""
+    w = W.c2_2d_vhs()
+    d, N, M, S, gamma = w.d, w.N, w.M, w.S, w.gamma
+    ft = O.project(w, d, N, S, 1).ravel()
+    modes = sample_modes(d, N, 48, seed=11)
+    gain, loss = O.collide_parts(ft, d, N, M, S, gamma, r=1, modes=modes)
+    Q, info, mom = gpu_collide(ft, d, N, M, S, gamma, 1e-6, precision=PG_PREC_FP32)
+    assert info["points"] == M * N ** (2 * d)
+    assert rel_l2(Q[flat_index(modes, N)], gain - loss) < TOL32
+    ma, en = O.mass_energy_coeffs(d, N, S)
+    assert abs(mom["mass"]) <= 1e-6 * abs(mom["mass_gain"])
+
+
+def test_projection_matches_oracle():
+    import torch
+    from paper_2105_08806_gb300 import Plan
+    for d, N, S, map_log in ((2, 16, 2.0, False), (3, 6, 2.5, True)):
+        r = 0 if map_log else 1
+        fun = _maxwell3(d, 5)
+        with Plan(d, N, 4, S, 0.0, 1e-6, map_log=map_log) as plan:
+            v = np.array(plan.project_nodes())
+            grids = np.meshgrid(*([v] * d), indexing="ij")
+            fv = fun(np.stack([g.ravel() for g in grids], 1))
+            fdev = torch.as_tensor(fv, device="cuda")
+            out = torch.empty((N + 1) ** d, dtype=torch.float64, device="cuda")
+            plan.project(fdev, out)
+            torch.cuda.synchronize()
+        ref = O.project(fun, d, N, S, r, Mp=len(v)).ravel()
+        assert rel_l2(out.cpu().numpy(), ref) < 1e-12
+
+
+def test_quadratic_scaling_and_zero():
+    d, N, M, S = 2, 10, 8, 2.0
+    ft = O.project(_maxwell3(d, 1), d, N, S, 1).ravel()
+    Q1, _, _ = gpu_collide(ft, d, N, M, S, 1.0, 1e-13, precision=PG_PREC_FP64)
+    Q3, _, _ = gpu_collide(3 * ft, d, N, M, S, 1.0, 1e-13, precision=PG_PREC_FP64)
+    assert rel_l2(Q3, 9 * Q1) < 1e-12
+    Q0, _, _ = gpu_collide(np.zeros_like(ft), d, N, M, S, 1.0, 1e-13, precision=PG_PREC_FP64)
+    assert np.all(Q0 == 0)
+
+
+def test_non_default_stream_and_repeat():
+    """Two calls on a side stream give the same Q (up to atomic summation order)."""
+    import torch
+    from paper_2105_08806_gb300 import Plan
+    d, N, M, S = 2, 12, 8, 2.0
+    ft = O.project(_maxwell3(d, 2), d, N, S, 1).ravel()
+    s = torch.cuda.Stream()
+    f = torch.as_tensor(ft, device="cuda")
+    Q1 = torch.empty_like(f)
+    Q2 = torch.empty_like(f)
+    with Plan(d, N, M, S, 0.0, 1e-6) as plan:
+        plan.set_stream(s)
+        with torch.cuda.stream(s):
+            plan.collide(f, Q1)
+            plan.collide(f, Q2)
+        s.synchronize()
+    assert rel_l2(Q2.cpu().numpy(), Q1.cpu().numpy()) < 1e-6
+    ref = O.collide(ft, d, N, M, S, 0.0)
+    assert rel_l2(Q1.cpu().numpy(), ref) < TOL32
+
+
+def test_stage_timing():
+    import torch
+    from paper_2105_08806_gb300 import Plan
+    d, N, M, S = 2, 16, 8, 2.0
+    f = torch.as_tensor(O.project(W.c1_2d_maxwell(), d, N, S, 1).ravel(), device="cuda")
+    Q = torch.empty_like(f)
+    with Plan(d, N, M, S, 0.0, 1e-13) as plan:
+        plan.set_timing(True)
+        plan.collide(f, Q)
+        t = plan.stage_times()
+    assert len(t) == 4 and all(x >= 0 for x in t) and t[2] > 0
+
+
+def test_alloc_failure_injection_leaves_no_plan():
+    from paper_2105_08806_gb300 import PGBoltzError, Plan, lib
+    for k in (1, 5, 12):
+        lib().pg_boltz_debug_fail_alloc(k)
+        with pytest.raises(PGBoltzError) as ei:
+            Plan(2, 8, 8, 2.0, 0.0, 1e-6)
+        assert "injected" in str(ei.value)
+    lib().pg_boltz_debug_fail_alloc(0)
+    with Plan(2, 8, 8, 2.0, 0.0, 1e-6):
+        pass
