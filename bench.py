@@ -6,7 +6,7 @@ generation + spreading, cosine transform + deconvolution, combine) for the 2D
 hard-sphere workload: d = 2, N = 64 (65^2 modes), M = 32 circle points, S = 3,
 gamma = 1, algebraic map, f = three Maxwellians + a Gaussian-windowed positive
 perturbation (seeded synthetic input, projected on the GPU).  The headline arm is
-the FP32-spreading path (tol 1e-6, FP64 loss / transform / deconvolution); the
+the FP32-spreading path (tol 1e-7, FP64 loss / transform / deconvolution); the
 FP64-spreading path is timed beside it.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--tol32", type=float, default=1e-7)
+    ap.add_argument("--upsampfac", type=float, default=0.0)
     return ap.parse_args()
 
 
@@ -153,7 +155,7 @@ def run_ours(args):
     w = Wl.c2_2d_vhs()
     d, N, M, S, gamma = w.d, w.N, w.M, w.S, w.gamma
     stream = torch.cuda.Stream(device=dev)
-    plan32 = Plan(d, N, M, S, gamma, 1e-6, precision=PG_PREC_FP32)
+    plan32 = Plan(d, N, M, S, gamma, args.tol32, precision=PG_PREC_FP32, upsampfac=args.upsampfac)
     plan64 = Plan(d, N, M, S, gamma, 1e-13, precision=PG_PREC_FP64)
     for p in (plan32, plan64):
         p.set_stream(stream)
@@ -263,7 +265,8 @@ def run_ours(args):
         "data": "synthetic (seeded three-Maxwellian + perturbation density, projected on the GPU)",
         "config": {
             "workload": "2D hard spheres (gamma=1), N=64 (65^2 modes), M=32 circle points, S=3, algebraic map",
-            "spread_precision": "fp32 (tol 1e-6); loss, transform, deconvolution fp64",
+            "spread_precision": f"fp32 (tol {args.tol32:g}); loss, transform, deconvolution fp64",
+            "upsampfac": info32["upsampfac"],
             "kernel_width": wgt, "n_grid": info32["n_grid"], "n_fold": info32["n_fold"],
             "points_per_eval": info32["points"], "spread_blocks": info32["spread_blocks"],
             "l2": "flushed between timed steps (256 MiB write, outside the step events)",

@@ -75,6 +75,9 @@ typedef struct {
     int proj_nodes;      /* Chebyshev-Gauss nodes per axis for pg_boltz_project, 0 -> 4(N+1) */
     int spread_threads;  /* threads per spreading block, 0 -> automatic                  */
     int spread_blocks_per_sm; /* spreading blocks per SM, 0 -> automatic                 */
+    int screen;          /* 1: skip node pairs whose strength bound is below 1e-3 tol B / N^(2d),
+                            B >= sum of all point strengths; the skipped strength is at most
+                            1e-3 tol B.  0 (default): spread every pair.                     */
 } pg_boltz_opts_t;
 
 /* Read-only description of a plan (pg_boltz_info). */

@@ -27,18 +27,33 @@ struct SpreadArgs {
     const void *a;        // nnode values a_i = W_i g_i
     const void *sig;      // M x d sphere points
     const void *wsig;     // M sphere weights
-    double *grid;         // nf^d folded grid, FP64, accumulated with atomics
+    double Wsig;          // sum_m w_m
+    const double *bound;  // device scalar B >= sum_p |q_p| (written by the loss kernel)
+    double prune_rel;     // pairs whose strength bound is below prune_rel * B / npairs are skipped (0: none)
+    unsigned long long *grid;  // nf^d folded grid, int64 fixed point in units of 2^-Eg
 };
 
-// Launch the spreading kernel for (T, d, w); returns cudaSuccess or the launch error.
-cudaError_t launch_spread_f32(const SpreadArgs &a, int w, int blocks, int threads, size_t smem,
-                              cudaStream_t s);
-cudaError_t launch_spread_f64(const SpreadArgs &a, int w, int blocks, int threads, size_t smem,
-                              cudaStream_t s);
+// Exponent Eg of the grid's fixed-point unit 2^-Eg: the largest E with B 2^E < 2^61 for the
+// bound B >= sum_p |q_p| (0 when B is zero or not finite).
+__host__ __device__ inline int global_exponent(double B)
+{
+    if (!(B > 0.0) || !(B < 1.0e300)) return 0;
+    return 60 - ilogb(B);
+}
+
+// Launch the spreading kernel for (precision, d, w); returns cudaSuccess or the launch error.
+// One translation unit per (precision, d) keeps the parallel build short.
+cudaError_t launch_spread_f32_d2(const SpreadArgs &a, int w, int blocks, int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_spread_f32_d3(const SpreadArgs &a, int w, int blocks, int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_spread_f64_d2(const SpreadArgs &a, int w, int blocks, int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_spread_f64_d3(const SpreadArgs &a, int w, int blocks, int threads, size_t smem, cudaStream_t s);
 // Highest kernel width with a compiled spreading kernel for each type.
 constexpr int kMaxWidthF32 = 10;
 constexpr int kMaxWidthF64 = 16;
 constexpr int kMinWidth = 2;
+// Largest spreading block for each type (the kernels' launch bounds).
+constexpr int kMaxThreadsF32 = 1024;
+constexpr int kMaxThreadsF64 = 256;
 
 // Three-axis shape of a C-order array; 2D arrays use e0 = 1.
 struct Dims3 {
@@ -52,10 +67,17 @@ cudaError_t launch_axis_pass(const double *in, Dims3 in_dims, int ax, const doub
 // writes a (FP64) and, if af != nullptr, a float copy.
 cudaError_t launch_recon_last(const double *in, Dims3 in_dims, const double *A, int m,
                               const double *scale, int d, double *a, float *af, cudaStream_t s);
-// Loss: h_i = a_i * Lsum_i * prod_l inv_mu2[i_l], Lsum_i = Bw * sum_j a_j B(|v_i - v_j|).
+// Loss: h_i = a_i * Lsum_i * prod_l inv_mu2[i_l], Lsum_i = Bw * sum_j a_j B(|v_i - v_j|);
+// also ub_i = |a_i| Bw sum_j |a_j| B_ij prod_l mu^-2(|c_l| + rad), an upper bound of the
+// spreading strengths of the pairs (i, .).
 cudaError_t launch_loss(const double *a, const double *vnode, int N, int d, double gamma,
-                        int fast_gamma, double Bw, const double *inv_mu2, double *h,
-                        cudaStream_t s);
+                        int fast_gamma, double Bw, const double *inv_mu2, double S, int r,
+                        double *h, double *ub, cudaStream_t s);
+// B = sum_i ub_i (fixed summation order), written to *B.
+cudaError_t launch_bound_reduce(const double *ub, int n, double *B, cudaStream_t s);
+// First transform pass reading the int64 fixed-point grid (units 2^-Eg, Eg from *B).
+cudaError_t launch_axis_pass_fixed(const unsigned long long *in, Dims3 in_dims, int ax, const double *A,
+                                   int m, const double *B, double *out, cudaStream_t s);
 // Final pass along axis 2: Qp = D . G, Qm = E . H, Q = Qp - Qm (also copied to Qcopy).
 cudaError_t launch_final(const double *G, Dims3 g_dims, const double *D, const double *H,
                          Dims3 h_dims, const double *E, int m, double *Q, double *Qplus,

@@ -139,7 +139,11 @@ struct pg_boltz_plan_s {
     double *tA = nullptr, *tB = nullptr, *tC = nullptr, *tD = nullptr;
     double *a64 = nullptr;
     float *a32 = nullptr;
-    double *h = nullptr, *grid = nullptr, *Qplus = nullptr, *Qlast = nullptr, *mom = nullptr;
+    double *h = nullptr, *Qplus = nullptr, *Qlast = nullptr, *mom = nullptr;
+    double *ub = nullptr;      // N^d per-node strength bounds
+    double *bound = nullptr;   // scalar B >= sum_p |q_p| (follows the grid in one allocation)
+    unsigned long long *grid = nullptr;  // folded grid, int64 fixed point
+    double prune_rel = 0.0;
 };
 
 namespace {
@@ -353,28 +357,38 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
         (rc = dev_alloc(p, (void **)&p->a64, (size_t)p->nnode * 8)) ||
         (rc = dev_alloc(p, (void **)&p->a32, (size_t)p->nnode * 4)) ||
         (rc = dev_alloc(p, (void **)&p->h, (size_t)p->nnode * 8)) ||
-        (rc = dev_alloc(p, (void **)&p->grid, grid_cells * 8)) ||
+        (rc = dev_alloc(p, (void **)&p->grid, grid_cells * 8 + 8)) ||
+        (rc = dev_alloc(p, (void **)&p->ub, (size_t)p->nnode * 8)) ||
         (rc = dev_alloc(p, (void **)&p->Qplus, modes * 8)) || (rc = dev_alloc(p, (void **)&p->Qlast, modes * 8)) ||
         (rc = dev_alloc(p, (void **)&p->mom, 8 * 8)))
         return rc;
+    p->bound = reinterpret_cast<double *>(p->grid + grid_cells);
 
     // ---- spreading launch shape
     cudaDeviceProp prop;
     cudaError_t e = cudaGetDeviceProperties(&prop, p->device);
     if (e != cudaSuccess) return set_error(PG_ERR_CUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e));
-    const size_t elem = (p->prec == PG_PREC_FP32) ? 4 : 8;
+    const size_t elem = 8;  // two 32-bit words per cell (64-bit fixed point), both precisions
     const size_t plane = (size_t)nfd1;
-    const size_t max_smem = prop.sharedMemPerBlockOptin;
+    const size_t max_smem = prop.sharedMemPerBlockOptin - 1024;  // leave room for the kernels' static shared memory
     int rows_fit = (int)std::min<size_t>(p->nf, max_smem / (plane * elem));
     if (rows_fit < 1) return set_error(PG_ERR_ARG, "folded grid plane of %zu cells does not fit shared memory", plane);
     p->nslab = (p->nf + rows_fit - 1) / rows_fit;
     p->rows_per_slab = (p->nf + p->nslab - 1) / p->nslab;
     p->nslab = (p->nf + p->rows_per_slab - 1) / p->rows_per_slab;  // no empty trailing slab
     p->spread_smem = (size_t)p->rows_per_slab * plane * elem;
-    p->spread_threads = (o.spread_threads > 0) ? o.spread_threads : 256;
-    if (p->spread_threads % 32 || p->spread_threads > 256)
-        return set_error(PG_ERR_ARG, "spread_threads must be a multiple of 32 and <= 256");
-    int per_sm = (int)(prop.sharedMemPerMultiprocessor / (p->spread_smem + prop.reservedSharedMemPerBlock));
+    const int max_threads = (p->prec == PG_PREC_FP32) ? pgb::kMaxThreadsF32 : pgb::kMaxThreadsF64;
+    int per_sm = (int)(prop.sharedMemPerMultiprocessor / (p->spread_smem + 1024 + prop.reservedSharedMemPerBlock));
+    per_sm = std::max(per_sm, 1);
+    if (o.spread_threads > 0) {
+        p->spread_threads = o.spread_threads;
+    } else {
+        // about 1024 resident threads per SM (the kernels use up to 64 registers)
+        int t = (1024 / per_sm) / 32 * 32;
+        p->spread_threads = std::max(128, std::min(max_threads, t));
+    }
+    if (p->spread_threads % 32 || p->spread_threads > max_threads)
+        return set_error(PG_ERR_ARG, "spread_threads must be a multiple of 32 and <= %d", max_threads);
     per_sm = std::min(per_sm, prop.maxThreadsPerMultiProcessor / p->spread_threads);
     if (o.spread_blocks_per_sm > 0) per_sm = std::min(per_sm, o.spread_blocks_per_sm);
     per_sm = std::max(per_sm, 1);
@@ -401,6 +415,7 @@ int validate(const pg_boltz_opts_t &o)
     if (o.upsampfac != 0.0 && !(o.upsampfac >= 1.5 && o.upsampfac <= 4.0))
         return set_error(PG_ERR_ARG, "upsampfac must be in [1.5, 4] (got %g)", o.upsampfac);
     if (o.proj_nodes < 0 || o.proj_nodes > 4096) return set_error(PG_ERR_ARG, "proj_nodes out of range");
+    if (o.screen != 0 && o.screen != 1) return set_error(PG_ERR_ARG, "screen must be 0 or 1");
     return PG_OK;
 }
 
@@ -482,6 +497,7 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_ex(const pg_boltz_opts_t *opts)
     p->r = o.map_log ? 0 : 1;
     p->prec = (o.precision == PG_PREC_AUTO) ? (o.tol < 1e-8 ? PG_PREC_FP64 : PG_PREC_FP32) : o.precision;
     p->info.sphere = (o.d == 3) ? (o.sphere == PG_SPHERE_AUTO ? PG_SPHERE_ANTIPODAL : o.sphere) : PG_SPHERE_AUTO;
+    p->prune_rel = o.screen ? 1e-3 * o.tol : 0.0;
     if (build_plan(p, o)) {
         free_plan(p);
         return nullptr;
@@ -507,7 +523,7 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_ex(const pg_boltz_opts_t *opts)
     in.pairs = p->npairs;
     in.points = p->npairs * p->M;
     in.proj_nodes = p->Mp;
-    in.launches_per_collide = 5 + 3 * (p->d - 1);
+    in.launches_per_collide = 3 + 3 * p->d;
     in.device_bytes = p->device_bytes;
     return p;
 }
@@ -559,16 +575,19 @@ PG_API int pg_boltz_collide(pg_boltz_plan_t *p, const double *f_dev, double *Q_d
         return rc;
     ++launches;
     mark(1);
-    // 2. loss weights h_i = a_i L_i / mu_i^2   (Eq. Qminus, inner sum over v_*, sigma)
+    // 2. clear the fixed-point grid and its bound; loss weights h_i = a_i L_i / mu_i^2 (Eq. Qminus,
+    //    inner sum over v_*, sigma) and the strength bound B >= sum_p |q_p|
+    const size_t grid_bytes = (size_t)ipow(p->nf, d) * 8;
+    if ((rc = cuda_check(cudaMemsetAsync(p->grid, 0, grid_bytes + 8, p->stream), "memset grid"))) return rc;
+    ++launches;
     if ((rc = cuda_check(pgb::launch_loss(p->a64, p->v64, N, d, p->gamma, p->fast_gamma, p->Bconst * p->Wsig,
-                                          p->inv_mu2, p->h, p->stream), "loss")))
+                                          p->inv_mu2, p->S, p->r, p->h, p->ub, p->stream), "loss")))
         return rc;
+    ++launches;
+    if ((rc = cuda_check(pgb::launch_bound_reduce(p->ub, p->nnode, p->bound, p->stream), "bound"))) return rc;
     ++launches;
     mark(2);
     // 3. spread the M N^(2d) post-collision points onto the folded grid   (Eq. num_fast_k, Eq. nufft)
-    const size_t grid_bytes = (size_t)ipow(p->nf, d) * 8;
-    if ((rc = cuda_check(cudaMemsetAsync(p->grid, 0, grid_bytes, p->stream), "memset grid"))) return rc;
-    ++launches;
     pgb::SpreadArgs sa;
     sa.d = d;
     sa.N = N;
@@ -590,16 +609,33 @@ PG_API int pg_boltz_collide(pg_boltz_plan_t *p, const double *f_dev, double *Q_d
     sa.a = f32 ? (const void *)p->a32 : (const void *)p->a64;
     sa.sig = f32 ? (const void *)p->sig32 : (const void *)p->sig64;
     sa.wsig = f32 ? (const void *)p->wsig32 : (const void *)p->wsig64;
+    sa.Wsig = p->Wsig;
+    sa.bound = p->bound;
+    sa.prune_rel = p->prune_rel;
     sa.grid = p->grid;
-    cudaError_t e = f32 ? pgb::launch_spread_f32(sa, p->w, p->spread_blocks, p->spread_threads, p->spread_smem, p->stream)
-                        : pgb::launch_spread_f64(sa, p->w, p->spread_blocks, p->spread_threads, p->spread_smem, p->stream);
+    auto launch = f32 ? (d == 2 ? pgb::launch_spread_f32_d2 : pgb::launch_spread_f32_d3)
+                      : (d == 2 ? pgb::launch_spread_f64_d2 : pgb::launch_spread_f64_d3);
+    cudaError_t e = launch(sa, p->w, p->spread_blocks, p->spread_threads, p->spread_smem, p->stream);
     if ((rc = cuda_check(e, "spread"))) return rc;
     ++launches;
     mark(3);
-    // 4. cosine transform + deconvolution of the grid, forward Chebyshev transform of the loss
+    // 4. cosine transform + deconvolution of the grid (first pass converts from fixed point),
+    //    forward Chebyshev transform of the loss
     pgb::Dims3 gd = dims_of(d, p->nf, p->nf, p->nf);
-    const double *gcur = nullptr;
-    if ((rc = leading_passes(p, p->grid, gd, p->Dm, N + 1, p->tA, p->tB, &gcur, &launches))) return rc;
+    const int ax0 = 3 - d;
+    if ((rc = cuda_check(pgb::launch_axis_pass_fixed(p->grid, gd, ax0, p->Dm, N + 1, p->bound, p->tA, p->stream),
+                         "transform pass")))
+        return rc;
+    ++launches;
+    gd.e[ax0] = N + 1;
+    const double *gcur = p->tA;
+    if (d == 3) {
+        if ((rc = cuda_check(pgb::launch_axis_pass(p->tA, gd, 1, p->Dm, N + 1, p->tB, p->stream), "transform pass")))
+            return rc;
+        ++launches;
+        gd.e[1] = N + 1;
+        gcur = p->tB;
+    }
     pgb::Dims3 hd = dims_of(d, N, N, N);
     const double *hcur = nullptr;
     if ((rc = leading_passes(p, p->h, hd, p->E, N + 1, p->tC, p->tD, &hcur, &launches))) return rc;

@@ -1,17 +1,16 @@
 // Spreading kernel templates shared by the FP32 and FP64 translation units.
-#pragma once
-// Fused post-collision point generation + exponential-of-semicircle spreading
-// onto the folded cosine grid (Section 4.2, Eq. num_fast_k and Eq. nufft).
+//
+// Fused post-collision point generation + exponential-of-semicircle spreading onto
+// the folded cosine grid (Section 4.2, Eq. num_fast_k and Eq. nufft).
 //
 // One thread owns one node pair (i, j) and walks the M sphere points sigma_m:
 //   v'     = (v_i + v_j)/2 + |v_i - v_j| sigma_m / 2
 //   z_l    = arccos(xi(v'_l))                     angle of the l-th mapped coordinate
 //   q      = a_i a_j B(|v_i - v_j|) w_m prod_l mu(xi(v'_l))^-2
-// and adds q prod_l psi(x_{g_l} - z_l) to the w^d cells of the folded grid
-// around z.  The gain coefficient is the cosine sum sum_p q_p prod_l cos(k_l z_pl);
-// cos is even and 2 pi periodic, so the periodic grid of n cells can be folded
-// onto its n/2 + 1 cells g = 0..n/2 (cell u and cell n - u carry the same cosine):
-// every unfolded support index u is added at fold(u) = min(u mod n, n - u mod n).
+// and adds q prod_l psi(x_{g_l} - z_l) to the w^d cells of the folded grid around z.
+// The gain coefficient is the cosine sum sum_p q_p prod_l cos(k_l z_pl); cos is even
+// and 2 pi periodic, so the periodic grid of n cells folds onto its n/2 + 1 cells
+// g = 0..n/2: every unfolded support index u is added at fold(u) = min(u mod n, n - u mod n).
 //
 // Stable forms of the angle and the weight from the map formulas of Section 2.1:
 //   r = 1 (algebraic):   cos z = v/sqrt(S^2+v^2), sin z = S/sqrt(S^2+v^2)
@@ -19,10 +18,28 @@
 //   r = 0 (logarithmic): cos z = tanh(v/S), sin z = sech(v/S)
 //                        -> z = atan2(1, sinh(v/S)), mu^-2 = S cosh(v/S)
 //
-// Each block accumulates in a private shared-memory copy of a slab of the
-// folded grid (all of it when it fits) with shared-memory atomics, then adds
-// the slab to the FP64 global grid.  Points whose axis-0 support misses the
-// block's slab are skipped after their first coordinate is formed.
+// Accumulation:
+//  - the global folded grid holds int64 values in units of 2^-Eg, where B >= sum_p |q_p|
+//    (an upper bound written by the loss kernel) and B 2^Eg <= 2^61: no cell can overflow,
+//    and block partial sums add exactly and in any order;
+//  - FP64 kernel: each block adds into a private FP64 copy of its slab of the grid in shared
+//    memory; at the end each cell's partial sum is rounded to the grid unit (relative error
+//    2^-61 B) and added to the global grid.
+//  - FP32 kernel: the private copy is 64-bit fixed point kept as two 32-bit words per cell
+//    (lo, unsigned; hi, signed) in units of 2^-Et, Et = Eg - 10:
+//    a contribution x (int64) is added to lo with one native 32-bit shared atomic; the
+//    carry of that addition (from the returned old value) plus the high half of x goes to
+//    hi with a second atomic only when it is non-zero.  The unit is chosen so typical
+//    contributions fit in ~22 bits, so the second atomic is rare.  Atomic additions on lo are
+//    serialised, so every carry is the carry of exactly that addition and hi:lo ends as the
+//    exact two's-complement sum.  (Floating-point shared atomics are compare-and-swap loops
+//    and their rounding limits FP32 accuracy; 64-bit integer shared atomics are several
+//    times slower than 32-bit ones.)
+//    At the end each block adds its slab (hi:lo scaled by 2^10) to the global grid.  Each
+//    contribution is rounded once, to the tile unit; all later additions are exact.
+#pragma once
+
+#include <climits>
 #include <cuda_runtime.h>
 
 #include "pgb_internal.cuh"
@@ -63,9 +80,8 @@ __device__ __forceinline__ int fold_index(int u, int n)
     return (g > (n >> 1)) ? n - g : g;
 }
 
-// The w kernel weights psi(x_u - z) of one axis, u = s..s+w-1, in units where
-// one grid cell is 1 and x = z n / (2 pi): psi = exp(beta (sqrt(1 - t^2) - 1)),
-// t = (u - x) * 2 / w.  Fold indices go to idx[].
+// The w kernel weights psi(x_u - z) of one axis, u = s..s+w-1, in units where one grid
+// cell is 1 and x = z n / (2 pi): psi = exp(beta (sqrt(1 - t^2) - 1)), t = (u - x) 2/w.
 template <typename T, int W>
 __device__ __forceinline__ void axis_weights(T x, T beta, int n, T *wt, int *idx)
 {
@@ -80,168 +96,314 @@ __device__ __forceinline__ void axis_weights(T x, T beta, int n, T *wt, int *idx
     }
 }
 
-template <typename T, int D, int W>
-__global__ void __launch_bounds__(256) k_spread(const SpreadArgs p)
+// Add one contribution x (already in tile units) to cell c of the split tile.
+__device__ __forceinline__ void add_split(unsigned *lo, int *hi, int c, long long x)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *tile = reinterpret_cast<T *>(smem_raw);
-
-    const int nf = p.nf;
-    const int n = p.n;
-    const int plane = (D == 3) ? nf * nf : nf;  // cells in one axis-0 row
-    const int slab = blockIdx.x % p.nslab;
-    const int row_lo = slab * p.rows_per_slab;
-    const int row_hi = min(row_lo + p.rows_per_slab, nf);
-    const int nrows = row_hi - row_lo;
-    if (nrows <= 0) return;  // uniform over the block: an empty trailing slab does nothing
-    const int ncell = nrows * plane;
-    for (int c = threadIdx.x; c < ncell; c += blockDim.x) tile[c] = T(0);
-    __syncthreads();
-
-    const T *vnode = static_cast<const T *>(p.vnode);
-    const T *acoef = static_cast<const T *>(p.a);
-    const T *sig = static_cast<const T *>(p.sig);
-    const T *wsig = static_cast<const T *>(p.wsig);
-    const T S = T(p.S);
-    const T SS = S * S;
-    const T invS = T(1) / S;
-    const T gs = T(p.grid_scale);
-    const T beta = T(p.beta);
-    const T Bc = T(p.Bconst);
-    const T gam = T(p.gamma);
-    const int N = p.N;
-    const int nnode = p.nnode;
-    const int M = p.M;
-    const bool alg = (p.r == 1);
-
-    const long long groups = gridDim.x / p.nslab;
-    const long long stride = groups * blockDim.x;
-    for (long long pr = (long long)(blockIdx.x / p.nslab) * blockDim.x + threadIdx.x; pr < p.npairs;
-         pr += stride) {
-        const int i = (int)(pr / nnode);
-        const int j = (int)(pr - (long long)i * nnode);
-        T vi[D], vj[D], cen[D];
-        int ii = i, jj = j;
-#pragma unroll
-        for (int l = D - 1; l >= 0; --l) {
-            vi[l] = vnode[ii % N];
-            ii /= N;
-            vj[l] = vnode[jj % N];
-            jj /= N;
-        }
-        T g2 = T(0);
-#pragma unroll
-        for (int l = 0; l < D; ++l) {
-            const T dl = vi[l] - vj[l];
-            g2 += dl * dl;
-            cen[l] = T(0.5) * (vi[l] + vj[l]);
-        }
-        const T g = Fn<T>::sqrt_(g2);
-        T B;
-        switch (p.fast_gamma) {
-        case 0: B = Bc; break;
-        case 1: B = Bc * g; break;
-        case 2: B = Bc * Fn<T>::sqrt_(g); break;
-        default: B = Bc * Fn<T>::pow_(g, gam); break;
-        }
-        const T base = acoef[i] * acoef[j] * B;
-        if (base == T(0)) continue;
-        const T rad = T(0.5) * g;
-
-        for (int m = 0; m < M; ++m) {
-            T q = base * wsig[m];
-            T x[D];
-#pragma unroll
-            for (int l = 0; l < D; ++l) {
-                const T vp = cen[l] + rad * sig[m * D + l];
-                T z, m2;
-                if (alg) {
-                    z = Fn<T>::atan2_(S, vp);
-                    m2 = (SS + vp * vp) * invS;
-                } else {
-                    const T u = vp * invS;
-                    z = Fn<T>::atan2_(T(1), Fn<T>::sinh_(u));
-                    m2 = S * Fn<T>::cosh_(u);
-                }
-                q *= m2;
-                x[l] = z * gs;
-            }
-            T w0[W];
-            int r0[W];
-            axis_weights<T, W>(x[0], beta, n, w0, r0);
-            bool hit = false;
-#pragma unroll
-            for (int a = 0; a < W; ++a) {
-                r0[a] -= row_lo;
-                hit |= ((unsigned)r0[a] < (unsigned)nrows);
-                w0[a] *= q;
-            }
-            if (!hit) continue;
-            T w1[W];
-            int c1[W];
-            axis_weights<T, W>(x[1], beta, n, w1, c1);
-            if (D == 2) {
-#pragma unroll
-                for (int a = 0; a < W; ++a) {
-                    if ((unsigned)r0[a] >= (unsigned)nrows) continue;
-                    T *row = tile + r0[a] * plane;
-#pragma unroll
-                    for (int b = 0; b < W; ++b) atomicAdd(row + c1[b], w0[a] * w1[b]);
-                }
-            } else {
-                T w2[W];
-                int c2[W];
-                axis_weights<T, W>(x[D - 1], beta, n, w2, c2);
-#pragma unroll
-                for (int b = 0; b < W; ++b) c1[b] *= nf;
-                for (int a = 0; a < W; ++a) {
-                    if ((unsigned)r0[a] >= (unsigned)nrows) continue;
-                    T *row = tile + r0[a] * plane;
-#pragma unroll
-                    for (int b = 0; b < W; ++b) {
-                        const T wab = w0[a] * w1[b];
-                        T *line = row + c1[b];
-#pragma unroll
-                        for (int c = 0; c < W; ++c) atomicAdd(line + c2[c], wab * w2[c]);
-                    }
-                }
-            }
-        }
-    }
-    __syncthreads();
-    double *gdst = p.grid + (size_t)row_lo * plane;
-    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
-        const T v = tile[c];
-        if (v != T(0)) atomicAdd(gdst + c, (double)v);
+    if (x == 0) return;
+    const unsigned xl = (unsigned)x;
+    const unsigned old = atomicAdd(lo + c, xl);
+    const int carry = (old + xl < old) ? 1 : 0;
+    const int h = (int)(x >> 32) + carry;
+    if (h) atomicAdd(hi + c, h);
+}
+// FP32 contribution -> split tile: most contributions fit in 31 bits (the 32-bit conversion is
+// cheaper); larger ones take the 64-bit conversion.
+__device__ __forceinline__ void add_contrib(unsigned *lo, int *hi, int c, float x)
+{
+    if (fabsf(x) < 2147483648.0f) {
+        const int v = __float2int_rn(x);
+        if (v == 0) return;
+        const unsigned xl = (unsigned)v;
+        const unsigned old = atomicAdd(lo + c, xl);
+        const int h = ((v < 0) ? -1 : 0) + ((old + xl < old) ? 1 : 0);
+        if (h) atomicAdd(hi + c, h);
+    } else {
+        add_split(lo, hi, c, __float2ll_rn(x));
     }
 }
 
-template <typename T, int D, int W>
-cudaError_t launch_one(const SpreadArgs &a, int blocks, int threads, size_t smem, cudaStream_t s)
+template <typename T, int D>
+struct PairData {
+    T cen[D];  // (v_i + v_j)/2
+    T rad;     // |v_i - v_j|/2
+    T base;    // a_i a_j B(|v_i - v_j|)
+};
+
+// Load pair pr = i * nnode + j; false when its strength is zero.
+template <typename T, int D>
+__device__ __forceinline__ bool load_pair(const SpreadArgs &p, long long pr, PairData<T, D> &P)
 {
-    auto kern = k_spread<T, D, W>;
+    const int nnode = p.nnode, N = p.N;
+    const int i = (int)(pr / nnode);
+    const int j = (int)(pr - (long long)i * nnode);
+    const T *vnode = static_cast<const T *>(p.vnode);
+    const T *acoef = static_cast<const T *>(p.a);
+    const T aij = acoef[i] * acoef[j];
+    if (aij == T(0)) return false;
+    int ii = i, jj = j;
+    T g2 = T(0);
+#pragma unroll
+    for (int l = D - 1; l >= 0; --l) {
+        const T vi = vnode[ii % N], vj = vnode[jj % N];
+        ii /= N;
+        jj /= N;
+        const T dl = vi - vj;
+        g2 += dl * dl;
+        P.cen[l] = T(0.5) * (vi + vj);
+    }
+    const T g = Fn<T>::sqrt_(g2);
+    T B;
+    switch (p.fast_gamma) {
+    case 0: B = T(p.Bconst); break;
+    case 1: B = T(p.Bconst) * g; break;
+    case 2: B = T(p.Bconst) * Fn<T>::sqrt_(g); break;
+    default: B = T(p.Bconst) * Fn<T>::pow_(g, T(p.gamma)); break;
+    }
+    P.base = aij * B;
+    P.rad = T(0.5) * g;
+    return P.base != T(0);
+}
+
+// U >= sum_m |q_m|: |base| W_sigma prod_l mu^-2(|c_l| + rad), since |v'_l| <= |c_l| + rad and
+// mu^-2 grows with |v|.
+template <typename T, int D>
+__device__ __forceinline__ T pair_bound(const SpreadArgs &p, const PairData<T, D> &P)
+{
+    const T S = T(p.S), invS = T(1) / S;
+    T U = fabs(P.base) * T(p.Wsig);
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+        const T R = fabs(P.cen[l]) + P.rad;
+        U *= (p.r == 1) ? (S * S + R * R) * invS : S * Fn<T>::cosh_(R * invS);
+    }
+    return U;
+}
+
+// Spread the M points of one pair into the block tile; `sc` converts to tile units.
+// Shared-memory accumulators of the block tile.
+struct SplitTile {  // FP32 path: 64-bit fixed point as (lo, hi) 32-bit words
+    unsigned *lo;
+    int *hi;
+    __device__ __forceinline__ void add(int c, float x) const { add_contrib(lo, hi, c, x); }
+};
+struct DoubleTile {  // FP64 path: FP64 partial sums
+    double *v;
+    __device__ __forceinline__ void add(int c, double x) const
+    {
+        if (x != 0.0) atomicAdd(v + c, x);
+    }
+};
+
+template <typename T, int D, int W, typename Tile>
+__device__ __forceinline__ void spread_pair(const SpreadArgs &p, const PairData<T, D> &P, T sc, const Tile &tile,
+                                            int row_lo, int nrows, int plane)
+{
+    const T *sig = static_cast<const T *>(p.sig);
+    const T *wsig = static_cast<const T *>(p.wsig);
+    const T S = T(p.S), SS = S * S, invS = T(1) / S;
+    const T gs = T(p.grid_scale), beta = T(p.beta);
+    const int n = p.n, nf = p.nf;
+    const bool alg = (p.r == 1);
+    const T qbase = P.base * sc;
+    for (int m = 0; m < p.M; ++m) {
+        T q = qbase * wsig[m];
+        T x[D];
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+            const T vp = P.cen[l] + P.rad * sig[m * D + l];
+            T z, m2;
+            if (alg) {
+                z = Fn<T>::atan2_(S, vp);
+                m2 = (SS + vp * vp) * invS;
+            } else {
+                const T u = vp * invS;
+                z = Fn<T>::atan2_(T(1), Fn<T>::sinh_(u));
+                m2 = S * Fn<T>::cosh_(u);
+            }
+            q *= m2;
+            x[l] = z * gs;
+        }
+        T w0[W];
+        int r0[W];
+        axis_weights<T, W>(x[0], beta, n, w0, r0);
+        bool hit = false;
+#pragma unroll
+        for (int a = 0; a < W; ++a) {
+            r0[a] -= row_lo;
+            hit |= ((unsigned)r0[a] < (unsigned)nrows);
+            w0[a] *= q;
+        }
+        if (!hit) continue;
+        T w1[W];
+        int c1[W];
+        axis_weights<T, W>(x[1], beta, n, w1, c1);
+        if (D == 2) {
+#pragma unroll
+            for (int a = 0; a < W; ++a) {
+                if ((unsigned)r0[a] >= (unsigned)nrows) continue;
+                const int row = r0[a] * plane;
+#pragma unroll
+                for (int b = 0; b < W; ++b) tile.add(row + c1[b], w0[a] * w1[b]);
+            }
+        } else {
+            T w2[W];
+            int c2[W];
+            axis_weights<T, W>(x[D - 1], beta, n, w2, c2);
+#pragma unroll
+            for (int b = 0; b < W; ++b) c1[b] *= nf;
+            for (int a = 0; a < W; ++a) {
+                if ((unsigned)r0[a] >= (unsigned)nrows) continue;
+                const int row = r0[a] * plane;
+#pragma unroll
+                for (int b = 0; b < W; ++b) {
+                    const T wab = w0[a] * w1[b];
+                    const int line = row + c1[b];
+#pragma unroll
+                    for (int c = 0; c < W; ++c) tile.add(line + c2[c], wab * w2[c]);
+                }
+            }
+        }
+    }
+}
+
+struct SlabGeom {
+    int row_lo, nrows, plane, ncell;
+};
+
+__device__ __forceinline__ SlabGeom slab_geometry(const SpreadArgs &p, int D)
+{
+    SlabGeom g;
+    g.plane = (D == 3) ? p.nf * p.nf : p.nf;
+    const int slab = blockIdx.x % p.nslab;
+    g.row_lo = slab * p.rows_per_slab;
+    const int row_hi = min(g.row_lo + p.rows_per_slab, p.nf);
+    g.nrows = row_hi - g.row_lo;
+    g.ncell = g.nrows * g.plane;
+    return g;
+}
+
+// Pair numbering: the threads of one slab cover the pairs with stride `nthr`.  Lanes of a
+// warp take pairs nwarps apart (lane-major numbering), so the 32 points a warp spreads at
+// once come from unrelated (i, j) and rarely hit the same grid cells; neighbouring pairs
+// produce neighbouring points and would serialise the shared-memory atomics.
+__device__ __forceinline__ void pair_schedule(const SpreadArgs &p, long long &first, long long &nthr)
+{
+    const long long groups = gridDim.x / p.nslab;
+    nthr = groups * blockDim.x;
+    const long long nwarps = nthr >> 5;
+    const long long gwarp = (long long)(blockIdx.x / p.nslab) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    first = (long long)(threadIdx.x & 31) * nwarps + gwarp;
+}
+
+template <int D, int W>
+__global__ void __launch_bounds__(kMaxThreadsF32) k_spread_f32(const SpreadArgs p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SlabGeom G = slab_geometry(p, D);
+    if (G.nrows <= 0) return;  // uniform over the block: an empty trailing slab does nothing
+    SplitTile tile{reinterpret_cast<unsigned *>(smem_raw), reinterpret_cast<int *>(smem_raw) + G.ncell};
+    for (int c = threadIdx.x; c < G.ncell; c += blockDim.x) {
+        tile.lo[c] = 0u;
+        tile.hi[c] = 0;
+    }
+    __syncthreads();
+    const double Bnd = *p.bound;
+    const int Eg = global_exponent(Bnd);
+    // Tile unit 2^-Et with Et = Eg - 10 (still below 2^-50 B); kept inside the float range for
+    // tiny inputs (a coarser unit there).
+    const int Et = min(Eg - 10, 120);
+    const int shift = Eg - Et;
+    const float sc = (float)ldexp(1.0, Et);
+    const float tau = (float)(p.prune_rel * Bnd / (double)p.npairs);
+    long long first, nthr;
+    pair_schedule(p, first, nthr);
+    for (long long pr = first; pr < p.npairs; pr += nthr) {
+        PairData<float, D> P;
+        if (!load_pair<float, D>(p, pr, P)) continue;
+        if (tau > 0.0f && pair_bound<float, D>(p, P) < tau) continue;
+        spread_pair<float, D, W>(p, P, sc, tile, G.row_lo, G.nrows, G.plane);
+    }
+    __syncthreads();
+    unsigned long long *gdst = p.grid + (size_t)G.row_lo * G.plane;
+    for (int c = threadIdx.x; c < G.ncell; c += blockDim.x) {
+        const long long v = (long long)(((unsigned long long)(unsigned)tile.hi[c] << 32) | tile.lo[c]);
+        // |v 2^shift| <= B 2^Eg <= 2^61, so a non-zero v never comes with shift > 61
+        if (v && shift <= 62) atomicAdd(gdst + c, (unsigned long long)(v * (1ll << shift)));
+    }
+}
+
+template <int D, int W>
+__global__ void __launch_bounds__(kMaxThreadsF64) k_spread_f64(const SpreadArgs p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SlabGeom G = slab_geometry(p, D);
+    if (G.nrows <= 0) return;  // uniform over the block
+    DoubleTile tile{reinterpret_cast<double *>(smem_raw)};
+    for (int c = threadIdx.x; c < G.ncell; c += blockDim.x) tile.v[c] = 0.0;
+    __syncthreads();
+    const double Bnd = *p.bound;
+    const int Eg = global_exponent(Bnd);
+    const double tau = p.prune_rel * Bnd / (double)p.npairs;
+    long long first, nthr;
+    pair_schedule(p, first, nthr);
+    for (long long pr = first; pr < p.npairs; pr += nthr) {
+        PairData<double, D> P;
+        if (!load_pair<double, D>(p, pr, P)) continue;
+        if (tau > 0.0 && pair_bound<double, D>(p, P) < tau) continue;
+        spread_pair<double, D, W>(p, P, 1.0, tile, G.row_lo, G.nrows, G.plane);
+    }
+    __syncthreads();
+    // block partial sums -> the grid's fixed-point unit (|v| 2^Eg <= 2^61); the rounding of a
+    // partial sum is 2^-61 B at most
+    unsigned long long *gdst = p.grid + (size_t)G.row_lo * G.plane;
+    const double sc = ldexp(1.0, Eg);
+    for (int c = threadIdx.x; c < G.ncell; c += blockDim.x) {
+        const long long v = __double2ll_rn(tile.v[c] * sc);
+        if (v) atomicAdd(gdst + c, (unsigned long long)v);
+    }
+}
+
+template <int D, int W>
+cudaError_t launch_f32(const SpreadArgs &a, int blocks, int threads, size_t smem, cudaStream_t s)
+{
+    auto kern = k_spread_f32<D, W>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<blocks, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <typename T, int D, int W, int WMAX>
+template <int D, int W>
+cudaError_t launch_f64(const SpreadArgs &a, int blocks, int threads, size_t smem, cudaStream_t s)
+{
+    auto kern = k_spread_f64<D, W>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<blocks, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Compile-time dispatch on the kernel width w in [W, WMAX].
+template <bool F32, int D, int W, int WMAX>
 struct WidthDispatch {
-    static cudaError_t run(const SpreadArgs &a, int w, int blocks, int threads, size_t smem,
-                           cudaStream_t s)
+    static cudaError_t run(const SpreadArgs &a, int w, int blocks, int threads, size_t smem, cudaStream_t s)
     {
-        if (w == W) return launch_one<T, D, W>(a, blocks, threads, smem, s);
-        return WidthDispatch<T, D, W + 1, WMAX>::run(a, w, blocks, threads, smem, s);
+        if (w == W) {
+            if constexpr (F32) return launch_f32<D, W>(a, blocks, threads, smem, s);
+            else return launch_f64<D, W>(a, blocks, threads, smem, s);
+        }
+        return WidthDispatch<F32, D, W + 1, WMAX>::run(a, w, blocks, threads, smem, s);
     }
 };
 
-template <typename T, int D, int WMAX>
-struct WidthDispatch<T, D, WMAX, WMAX> {
-    static cudaError_t run(const SpreadArgs &a, int w, int blocks, int threads, size_t smem,
-                           cudaStream_t s)
+template <bool F32, int D, int WMAX>
+struct WidthDispatch<F32, D, WMAX, WMAX> {
+    static cudaError_t run(const SpreadArgs &a, int w, int blocks, int threads, size_t smem, cudaStream_t s)
     {
-        if (w == WMAX) return launch_one<T, D, WMAX>(a, blocks, threads, smem, s);
+        if (w == WMAX) {
+            if constexpr (F32) return launch_f32<D, WMAX>(a, blocks, threads, smem, s);
+            else return launch_f64<D, WMAX>(a, blocks, threads, smem, s);
+        }
         return cudaErrorInvalidValue;
     }
 };

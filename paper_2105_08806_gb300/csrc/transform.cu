@@ -90,12 +90,18 @@ __device__ double block_sum(double v)
 
 constexpr int kLossThreads = 128;
 
-// One block per outer node i:  Lsum_i = Bw sum_j a_j |v_i - v_j|^gamma, h_i = a_i Lsum_i / mu_i^2.
+// One block per outer node i:
+//   Lsum_i = Bw sum_j a_j |v_i - v_j|^gamma,   h_i = a_i Lsum_i / mu_i^2      (Eq. Qminus)
+//   ub_i   = |a_i| Bw sum_j |a_j| |v_i - v_j|^gamma prod_l mu^-2(|c_l| + rad)
+// where c = (v_i + v_j)/2, rad = |v_i - v_j|/2: every post-collision point of the pair lies
+// in the box |v'_l| <= |c_l| + rad and mu^-2 grows with |v|, so ub_i bounds the spreading
+// strengths sum_{j,m} |q_ijm| (times Bconst, which Bw carries).
 __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict__ a,
                                                         const double *__restrict__ vnode, int N,
                                                         int d, double gamma, int fast_gamma,
                                                         double Bw, const double *__restrict__ inv_mu2,
-                                                        double *__restrict__ h)
+                                                        double S, int r, double *__restrict__ h,
+                                                        double *__restrict__ ub)
 {
     const int nnode = (d == 2) ? N * N : N * N * N;
     const int i = blockIdx.x;
@@ -109,13 +115,15 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict_
     }
     double vi[3];
     for (int l = 0; l < 3; ++l) vi[l] = (l < d) ? vnode[idx[l]] : 0.0;
-    double acc = 0.0;
+    const double invS = 1.0 / S;
+    double acc = 0.0, bnd = 0.0;
     for (int j = threadIdx.x; j < nnode; j += blockDim.x) {
         int t = j;
-        double g2 = 0.0;
+        double g2 = 0.0, vj[3] = {0.0, 0.0, 0.0};
         for (int l = d - 1; l >= 0; --l) {
-            const double dl = vi[l] - vnode[t % N];
+            vj[l] = vnode[t % N];
             t /= N;
+            const double dl = vi[l] - vj[l];
             g2 += dl * dl;
         }
         double B;
@@ -126,12 +134,64 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict_
         default: B = (g2 > 0.0) ? pow(g2, 0.5 * gamma) : 0.0; break;
         }
         acc = fma(a[j], B, acc);
+        if (a[j] != 0.0 && B != 0.0) {
+            const double rad = 0.5 * sqrt(g2);
+            double mu = 1.0;
+            for (int l = 0; l < d; ++l) {
+                const double R = fabs(0.5 * (vi[l] + vj[l])) + rad;
+                mu *= (r == 1) ? (S * S + R * R) * invS : S * cosh(R * invS);
+            }
+            bnd = fma(fabs(a[j]) * B, mu, bnd);
+        }
     }
     const double tot = block_sum<kLossThreads>(acc);
+    const double tb = block_sum<kLossThreads>(bnd);
     if (threadIdx.x == 0) {
         double sc = 1.0;
         for (int l = 0; l < d; ++l) sc *= inv_mu2[idx[l]];
         h[i] = a[i] * Bw * tot * sc;
+        ub[i] = fabs(a[i]) * Bw * tb;
+    }
+}
+
+constexpr int kReduceThreads = 1024;
+
+// B = (1 + 1e-6) sum_i ub_i in a fixed order (deterministic); the factor covers FP32 rounding
+// of the strengths in the FP32 spreading kernel.
+__global__ void __launch_bounds__(kReduceThreads) k_bound_reduce(const double *__restrict__ ub, int n,
+                                                                  double *__restrict__ B)
+{
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += ub[i];
+    const double tot = block_sum<kReduceThreads>(s);
+    if (threadIdx.x == 0) *B = tot * (1.0 + 1e-6);
+}
+
+// First transform pass over the int64 fixed-point grid: out = (A . in) 2^-Eg.
+__global__ void k_axis_pass_fixed(const unsigned long long *__restrict__ in, Dims3 id, int ax,
+                                  const double *__restrict__ A, int m, const double *__restrict__ Bp,
+                                  double *__restrict__ out)
+{
+    Dims3 od = id;
+    od.e[ax] = m;
+    const long long total = (long long)od.e[0] * od.e[1] * od.e[2];
+    const int len = id.e[ax];
+    const long long sax = stride_of(id, ax);
+    const double unit = ldexp(1.0, -global_exponent(*Bp));
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < total;
+         o += (long long)gridDim.x * blockDim.x) {
+        int oc[3];
+        oc[2] = (int)(o % od.e[2]);
+        const long long t = o / od.e[2];
+        oc[1] = (int)(t % od.e[1]);
+        oc[0] = (int)(t / od.e[1]);
+        const int k = oc[ax];
+        oc[ax] = 0;
+        const long long base = ((long long)oc[0] * id.e[1] + oc[1]) * id.e[2] + oc[2];
+        const double *arow = A + (long long)k * len;
+        double acc = 0.0;
+        for (int s = 0; s < len; ++s) acc = fma(arow[s], (double)(long long)in[base + s * sax], acc);
+        out[o] = acc * unit;
     }
 }
 
@@ -237,10 +297,27 @@ cudaError_t launch_recon_last(const double *in, Dims3 in_dims, const double *A, 
 }
 
 cudaError_t launch_loss(const double *a, const double *vnode, int N, int d, double gamma,
-                        int fast_gamma, double Bw, const double *inv_mu2, double *h, cudaStream_t s)
+                        int fast_gamma, double Bw, const double *inv_mu2, double S, int r, double *h,
+                        double *ub, cudaStream_t s)
 {
     const int nnode = (d == 2) ? N * N : N * N * N;
-    k_loss<<<nnode, kLossThreads, 0, s>>>(a, vnode, N, d, gamma, fast_gamma, Bw, inv_mu2, h);
+    k_loss<<<nnode, kLossThreads, 0, s>>>(a, vnode, N, d, gamma, fast_gamma, Bw, inv_mu2, S, r, h, ub);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bound_reduce(const double *ub, int n, double *B, cudaStream_t s)
+{
+    k_bound_reduce<<<1, kReduceThreads, 0, s>>>(ub, n, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axis_pass_fixed(const unsigned long long *in, Dims3 in_dims, int ax, const double *A,
+                                   int m, const double *B, double *out, cudaStream_t s)
+{
+    Dims3 od = in_dims;
+    od.e[ax] = m;
+    k_axis_pass_fixed<<<grid_for((long long)od.e[0] * od.e[1] * od.e[2]), kThreads, 0, s>>>(in, in_dims, ax, A,
+                                                                                           m, B, out);
     return cudaGetLastError();
 }
 
