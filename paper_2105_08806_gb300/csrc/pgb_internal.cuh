@@ -31,6 +31,7 @@ struct SpreadArgs {
     const double *bound;  // device scalar B >= sum_p |q_p| (written by the loss kernel)
     double prune_rel;     // pairs whose strength bound is below prune_rel * B / npairs are skipped (0: none)
     unsigned long long *grid;  // nf^d folded grid, int64 fixed point in units of 2^-Eg
+    int simple_fold;      // 1 when w <= n/2: unfolded indices lie in [-n/2, n] (no modulo needed)
 };
 
 // Exponent Eg of the grid's fixed-point unit 2^-Eg: the largest E with B 2^E < 2^61 for the

@@ -119,6 +119,7 @@ struct pg_boltz_plan_s {
     std::vector<double> proj_v;  // host copy of projection node velocities
     bool have_q = false;
     int last_launches = 0;
+    pgb::SpreadArgs sargs{};   // spreading-kernel arguments (fixed at plan time)
     // optional per-stage timing: events recorded on the plan's stream around the stages
     bool timing = false;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -397,6 +398,35 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
     const long long need = ((p->npairs + p->spread_threads - 1) / p->spread_threads) * p->nslab;
     blocks = std::min(blocks, need);
     p->spread_blocks = (int)blocks;
+
+    // ---- spreading-kernel arguments
+    pgb::SpreadArgs &ka = p->sargs;
+    const bool f32 = (p->prec == PG_PREC_FP32);
+    ka.d = d;
+    ka.N = N;
+    ka.M = M;
+    ka.r = p->r;
+    ka.nnode = p->nnode;
+    ka.npairs = p->npairs;
+    ka.n = p->n;
+    ka.nf = p->nf;
+    ka.rows_per_slab = p->rows_per_slab;
+    ka.nslab = p->nslab;
+    ka.fast_gamma = p->fast_gamma;
+    ka.S = p->S;
+    ka.gamma = p->gamma;
+    ka.Bconst = p->Bconst;
+    ka.beta = p->beta;
+    ka.grid_scale = p->n / (2.0 * kPi);
+    ka.vnode = f32 ? (const void *)p->v32 : (const void *)p->v64;
+    ka.a = f32 ? (const void *)p->a32 : (const void *)p->a64;
+    ka.sig = f32 ? (const void *)p->sig32 : (const void *)p->sig64;
+    ka.wsig = f32 ? (const void *)p->wsig32 : (const void *)p->wsig64;
+    ka.Wsig = p->Wsig;
+    ka.bound = p->bound;
+    ka.prune_rel = p->prune_rel;
+    ka.grid = p->grid;
+    ka.simple_fold = (p->w <= p->n / 2) ? 1 : 0;
     return PG_OK;
 }
 
@@ -588,31 +618,7 @@ PG_API int pg_boltz_collide(pg_boltz_plan_t *p, const double *f_dev, double *Q_d
     ++launches;
     mark(2);
     // 3. spread the M N^(2d) post-collision points onto the folded grid   (Eq. num_fast_k, Eq. nufft)
-    pgb::SpreadArgs sa;
-    sa.d = d;
-    sa.N = N;
-    sa.M = p->M;
-    sa.r = p->r;
-    sa.nnode = p->nnode;
-    sa.npairs = p->npairs;
-    sa.n = p->n;
-    sa.nf = p->nf;
-    sa.rows_per_slab = p->rows_per_slab;
-    sa.nslab = p->nslab;
-    sa.fast_gamma = p->fast_gamma;
-    sa.S = p->S;
-    sa.gamma = p->gamma;
-    sa.Bconst = p->Bconst;
-    sa.beta = p->beta;
-    sa.grid_scale = p->n / (2.0 * kPi);
-    sa.vnode = f32 ? (const void *)p->v32 : (const void *)p->v64;
-    sa.a = f32 ? (const void *)p->a32 : (const void *)p->a64;
-    sa.sig = f32 ? (const void *)p->sig32 : (const void *)p->sig64;
-    sa.wsig = f32 ? (const void *)p->wsig32 : (const void *)p->wsig64;
-    sa.Wsig = p->Wsig;
-    sa.bound = p->bound;
-    sa.prune_rel = p->prune_rel;
-    sa.grid = p->grid;
+    const pgb::SpreadArgs &sa = p->sargs;
     auto launch = f32 ? (d == 2 ? pgb::launch_spread_f32_d2 : pgb::launch_spread_f32_d3)
                       : (d == 2 ? pgb::launch_spread_f64_d2 : pgb::launch_spread_f64_d3);
     cudaError_t e = launch(sa, p->w, p->spread_blocks, p->spread_threads, p->spread_smem, p->stream);

@@ -53,6 +53,8 @@ struct Fn;
 template <>
 struct Fn<float> {
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    // sqrt of x > 0 through the reciprocal square root (a few ulp; enough for FP32 weights)
+    static __device__ __forceinline__ float sqrt_pos(float x) { return x * rsqrtf(x); }
     static __device__ __forceinline__ float exp_(float x) { return __expf(x); }
     static __device__ __forceinline__ float atan2_(float y, float x) { return atan2f(y, x); }
     static __device__ __forceinline__ float sinh_(float x) { return sinhf(x); }
@@ -64,6 +66,7 @@ struct Fn<float> {
 template <>
 struct Fn<double> {
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double sqrt_pos(double x) { return sqrt(x); }
     static __device__ __forceinline__ double exp_(double x) { return exp(x); }
     static __device__ __forceinline__ double atan2_(double y, double x) { return atan2(y, x); }
     static __device__ __forceinline__ double sinh_(double x) { return sinh(x); }
@@ -80,19 +83,31 @@ __device__ __forceinline__ int fold_index(int u, int n)
     return (g > (n >> 1)) ? n - g : g;
 }
 
-// The w kernel weights psi(x_u - z) of one axis, u = s..s+w-1, in units where one grid
-// cell is 1 and x = z n / (2 pi): psi = exp(beta (sqrt(1 - t^2) - 1)), t = (u - x) 2/w.
+// Unfolded index u -> folded cell; `simple` when u is known to lie in [-n/2, n].
+__device__ __forceinline__ int fold_cell(int u, int n, bool simple)
+{
+    if (simple) {
+        u = (u < 0) ? -u : u;
+        return (u > (n >> 1)) ? n - u : u;
+    }
+    return fold_index(u, n);
+}
+
+// The w kernel weights psi(x_u - z) of one axis, u = s..s+w-1, in units where one grid cell
+// is 1 and x = z n / (2 pi): psi = exp(beta (sqrt(1 - t^2) - 1)), t = (u - x) 2/w.
 template <typename T, int W>
-__device__ __forceinline__ void axis_weights(T x, T beta, int n, T *wt, int *idx)
+__device__ __forceinline__ void axis_weights(const SpreadArgs &p, T x, T *wt, int *idx)
 {
     const int s = (int)Fn<T>::floor_(x - T(0.5 * W)) + 1;
     const T inv_hw = T(2.0 / W);
+    const T beta = T(p.beta);
+    const bool simple = p.simple_fold != 0;
 #pragma unroll
     for (int a = 0; a < W; ++a) {
         const T t = (T(s + a) - x) * inv_hw;
         const T one_m = T(1) - t * t;
-        wt[a] = one_m > T(0) ? Fn<T>::exp_(beta * (Fn<T>::sqrt_(one_m) - T(1))) : T(0);
-        idx[a] = fold_index(s + a, n);
+        wt[a] = one_m > T(0) ? Fn<T>::exp_(beta * (Fn<T>::sqrt_pos(one_m) - T(1))) : T(0);
+        idx[a] = fold_cell(s + a, p.n, simple);
     }
 }
 
@@ -107,12 +122,12 @@ __device__ __forceinline__ void add_split(unsigned *lo, int *hi, int c, long lon
     if (h) atomicAdd(hi + c, h);
 }
 // FP32 contribution -> split tile: most contributions fit in 31 bits (the 32-bit conversion is
-// cheaper); larger ones take the 64-bit conversion.
+// cheaper); larger ones take the 64-bit conversion.  Zero contributions are added too: a
+// branch around them costs more than the atomic.
 __device__ __forceinline__ void add_contrib(unsigned *lo, int *hi, int c, float x)
 {
     if (fabsf(x) < 2147483648.0f) {
         const int v = __float2int_rn(x);
-        if (v == 0) return;
         const unsigned xl = (unsigned)v;
         const unsigned old = atomicAdd(lo + c, xl);
         const int h = ((v < 0) ? -1 : 0) + ((old + xl < old) ? 1 : 0);
@@ -201,8 +216,8 @@ __device__ __forceinline__ void spread_pair(const SpreadArgs &p, const PairData<
     const T *sig = static_cast<const T *>(p.sig);
     const T *wsig = static_cast<const T *>(p.wsig);
     const T S = T(p.S), SS = S * S, invS = T(1) / S;
-    const T gs = T(p.grid_scale), beta = T(p.beta);
-    const int n = p.n, nf = p.nf;
+    const T gs = T(p.grid_scale);
+    const int nf = p.nf;
     const bool alg = (p.r == 1);
     const T qbase = P.base * sc;
     for (int m = 0; m < p.M; ++m) {
@@ -225,7 +240,7 @@ __device__ __forceinline__ void spread_pair(const SpreadArgs &p, const PairData<
         }
         T w0[W];
         int r0[W];
-        axis_weights<T, W>(x[0], beta, n, w0, r0);
+        axis_weights<T, W>(p, x[0], w0, r0);
         bool hit = false;
 #pragma unroll
         for (int a = 0; a < W; ++a) {
@@ -236,7 +251,7 @@ __device__ __forceinline__ void spread_pair(const SpreadArgs &p, const PairData<
         if (!hit) continue;
         T w1[W];
         int c1[W];
-        axis_weights<T, W>(x[1], beta, n, w1, c1);
+        axis_weights<T, W>(p, x[1], w1, c1);
         if (D == 2) {
 #pragma unroll
             for (int a = 0; a < W; ++a) {
@@ -248,7 +263,7 @@ __device__ __forceinline__ void spread_pair(const SpreadArgs &p, const PairData<
         } else {
             T w2[W];
             int c2[W];
-            axis_weights<T, W>(x[D - 1], beta, n, w2, c2);
+            axis_weights<T, W>(p, x[D - 1], w2, c2);
 #pragma unroll
             for (int b = 0; b < W; ++b) c1[b] *= nf;
             for (int a = 0; a < W; ++a) {
@@ -296,7 +311,7 @@ __device__ __forceinline__ void pair_schedule(const SpreadArgs &p, long long &fi
 }
 
 template <int D, int W>
-__global__ void __launch_bounds__(kMaxThreadsF32) k_spread_f32(const SpreadArgs p)
+__global__ void __launch_bounds__(kMaxThreadsF32) k_spread_f32(const __grid_constant__ SpreadArgs p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SlabGeom G = slab_geometry(p, D);
@@ -333,7 +348,7 @@ __global__ void __launch_bounds__(kMaxThreadsF32) k_spread_f32(const SpreadArgs 
 }
 
 template <int D, int W>
-__global__ void __launch_bounds__(kMaxThreadsF64) k_spread_f64(const SpreadArgs p)
+__global__ void __launch_bounds__(kMaxThreadsF64) k_spread_f64(const __grid_constant__ SpreadArgs p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SlabGeom G = slab_geometry(p, D);
