@@ -168,6 +168,39 @@ int pg_boltz_info(const pg_boltz_plan_t *plan, pg_boltz_info_t *out);
 void pg_boltz_destroy(pg_boltz_plan_t *plan);
 
 /*
+ * Size of the library-owned static device array used by pg_boltz_project_noalloc
+ * (4 MiB of doubles, held on every GPU that loads the library until process exit).
+ */
+#define PG_BOLTZ_NOALLOC_SCRATCH_BYTES (4u << 20)
+
+/*
+ * pg_boltz_project without any allocation.  The paper has no counterpart; this is a
+ * library facility for callers that cannot allocate device memory -- applications whose
+ * own pool or arena owns all device memory and forbids library calls to cudaMalloc, or
+ * bindings that can only pass pointers they already hold -- and therefore cannot create
+ * a plan (plans allocate their tables and workspace).
+ *
+ * Computes f~_k = (f, That_k) for 0 <= k_l <= N (Eq. MultiD_spectral_coef) by Chebyshev-Gauss
+ * quadrature with Mp nodes per axis, exactly as pg_boltz_project on a plan with the same
+ * d, N, S, map and proj_nodes = Mp (nodes from pg_boltz_project_nodes).
+ *   d: 2 or 3; N >= 2; S > 0; map_log: 0 algebraic (r = 1), 1 logarithmic (r = 0); Mp >= 1.
+ *   fvals_dev: device array of Mp^d doubles (f at the tensor grid of the nodes, C order).
+ *   ftilde_dev: device array of (N+1)^d doubles, written.
+ *   cuda_stream: a cudaStream_t (NULL = legacy default stream); the call is asynchronous.
+ * Scratch: (N+1) Mp + (N+1) Mp^(d-1) [+ (N+1)^2 Mp when d = 3] doubles of the static array of
+ * PG_BOLTZ_NOALLOC_SCRATCH_BYTES; larger requests return PG_ERR_ARG (see pg_boltz_last_error).
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress, with that device current) and
+ * caches it; make that first call before any stream capture.  All calls share the array,
+ * which keeps the last call's contents (every value a call reads it has written itself, so
+ * nothing needs clearing); calls that overlap on the GPU (different streams, or another
+ * host thread) race on it and must be serialised by the caller.
+ * Returns PG_OK, PG_ERR_ARG or PG_ERR_CUDA.
+ */
+int pg_boltz_project_noalloc(int d, int N, double S, int map_log, int Mp, const double *fvals_dev,
+                             double *ftilde_dev, void *cuda_stream);
+
+/*
  * Host-side fault injection for tests: the countdown-th device allocation made by a
  * later plan creation fails with PG_ERR_NOMEM (0 disables).  Process-wide; no device work.
  */

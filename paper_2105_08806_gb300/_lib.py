@@ -23,7 +23,7 @@ EXPORTS = (
     "pg_boltz_plan", "pg_boltz_plan_ex", "pg_boltz_set_stream", "pg_boltz_collide",
     "pg_boltz_moments", "pg_boltz_project_nodes", "pg_boltz_project", "pg_boltz_info",
     "pg_boltz_destroy", "pg_boltz_last_error", "pg_boltz_debug_fail_alloc", "pg_boltz_set_timing",
-    "pg_boltz_stage_times",
+    "pg_boltz_stage_times", "pg_boltz_project_noalloc",
 )
 
 

@@ -87,4 +87,7 @@ cudaError_t launch_final(const double *G, Dims3 g_dims, const double *D, const d
 cudaError_t launch_moments(const double *Q, const double *Qplus, int d, int N, double S,
                            double *out, cudaStream_t s);
 
+// Set the thread-local text returned by pg_boltz_last_error; returns code.
+int record_error(int code, const char *msg);
+
 }  // namespace pgb

@@ -100,6 +100,8 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
 
 }  // namespace
 
+int pgb::record_error(int code, const char *msg) { return set_error(code, "%s", msg); }
+
 struct pg_boltz_plan_s {
     pg_boltz_info_t info{};
     int device = 0;
