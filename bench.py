@@ -6,7 +6,7 @@ generation + spreading, cosine transform + deconvolution, combine) for the 2D
 hard-sphere workload: d = 2, N = 64 (65^2 modes), M = 32 circle points, S = 3,
 gamma = 1, algebraic map, f = three Maxwellians + a Gaussian-windowed positive
 perturbation (seeded synthetic input, projected on the GPU).  The headline arm is
-the FP32-spreading path (tol 1e-7, FP64 loss / transform / deconvolution); the
+the FP32-spreading path (tol 1e-6, FP64 loss / transform / deconvolution); the
 FP64-spreading path is timed beside it.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=3)
-    ap.add_argument("--tol32", type=float, default=1e-7)
+    ap.add_argument("--tol32", type=float, default=1e-6)
     ap.add_argument("--upsampfac", type=float, default=0.0)
     return ap.parse_args()
 
@@ -237,7 +237,8 @@ def run_ours(args):
     err = float(torch.linalg.norm(Q - Q64) / torch.linalg.norm(Q64))
     mom = plan64.moments()
 
-    # roofline of the dominant kernel (spreading): shared-memory read-modify-writes
+    # roofline of the dominant kernel (spreading): one shared-memory atomic add per
+    # contribution, M N^(2d) w^d contributions per launch
     spread_ms = statistics.mean(s[2] for s in st32)
     wgt = info32["kernel_width"]
     rmw_per_launch = info32["points"] * wgt ** d
@@ -245,6 +246,8 @@ def run_ours(args):
     sm_count = props.multi_processor_count
     peak_rmw = sm_count * 32 * 2.07e9  # one 32-lane shared-memory access per SM per clock at 2070 MHz
     achieved = rmw_per_launch / (spread_ms * 1e-3)
+    from paper_2105_08806_gb300._lib import probe_shared_atomics
+    measured_atomic = probe_shared_atomics(stream)
     stage_names = ["reconstruct", "loss", "spread", "transform"]
     stage_mean32 = {n: statistics.mean(s[i] for s in st32) for i, n in enumerate(stage_names)}
     stage_mean64 = {n: statistics.mean(s[i] for s in st64) for i, n in enumerate(stage_names)}
@@ -284,7 +287,10 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_rmw / 1e9,
                      "unit": "G shared-memory RMW/s", "frac": achieved / peak_rmw, "traffic": None,
                      "kernel": "k_spread<float,2,%d>" % wgt,
-                     "peak_basis": f"{sm_count} SMs x 32 shared-memory lanes/clk x 2070 MHz (derived)"},
+                     "peak_basis": f"{sm_count} SMs x 32 shared-memory lanes/clk x 2070 MHz (derived)",
+                     "measured_atomic_peak": measured_atomic / 1e9,
+                     "frac_of_measured_atomic_peak": achieved / measured_atomic,
+                     "measured_basis": "int32 shared atomics at random addresses, all SMs (pg_boltz_probe_shared_atomics)"},
         "e2e": {"value": world * 1000.0 / mean_e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * (N + 1) ** d,
                 "d2h_bytes_per_step": 8 * (N + 1) ** d},
         "gpu_launches": info32["launches_per_collide"] * args.steps,

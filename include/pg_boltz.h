@@ -75,9 +75,9 @@ typedef struct {
     int proj_nodes;      /* Chebyshev-Gauss nodes per axis for pg_boltz_project, 0 -> 4(N+1) */
     int spread_threads;  /* threads per spreading block, 0 -> automatic                  */
     int spread_blocks_per_sm; /* spreading blocks per SM, 0 -> automatic                 */
-    int screen;          /* 1: skip node pairs whose strength bound is below 1e-3 tol B / N^(2d),
-                            B >= sum of all point strengths; the skipped strength is at most
-                            1e-3 tol B.  0 (default): spread every pair.                     */
+    int screen;          /* 1: skip the node pairs with the smallest strength bounds, as many
+                            as keep their summed bound below 0.05 tol B (B >= the sum of all
+                            point strengths); 0 (default): spread every pair.               */
 } pg_boltz_opts_t;
 
 /* Read-only description of a plan (pg_boltz_info). */
@@ -166,6 +166,44 @@ int pg_boltz_info(const pg_boltz_plan_t *plan, pg_boltz_info_t *out);
 
 /* Free the plan and its device memory.  NULL-safe.  Synchronises the plan's stream. */
 void pg_boltz_destroy(pg_boltz_plan_t *plan);
+
+/*
+ * Batched plans: ncell independent operators of one dimension d (one velocity distribution
+ * per spatial cell of an inhomogeneous solver; each cell is an instance of Section 4.2 with its
+ * own N_c, M_c, S_c, gamma_c).  N[c], M[c], S[c], kernel_gamma[c]: host arrays of ncell values
+ * (2 <= N_c <= 200 in 2D, <= 40 in 3D; M_c even; the cell's folded grid must fit shared memory).
+ * The _ex form reads d, tol, map_log, precision, sphere, upsampfac, spread_threads,
+ * spread_blocks_per_sm and screen from opts (its N, M, S, kernel_gamma are ignored).
+ * NULL on error.  Other entry points accept a batched plan where noted.
+ */
+pg_boltz_plan_t *pg_boltz_plan_batched(int d, int ncell, const int *N, const int *M, const double *S,
+                                       const double *kernel_gamma, double tol);
+pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, int ncell, const int *N, const int *M,
+                                          const double *S, const double *kernel_gamma);
+
+/*
+ * Q for every cell of a batched plan.  f_packed_dev / Q_packed_dev: device arrays holding the
+ * cells' (N_c+1)^d coefficient arrays one after the other in cell order (offsets from
+ * pg_boltz_batched_offsets); they must not overlap.  Asynchronous on the plan's stream.  The
+ * launch sequence (prep, persistent spreading over a work queue of (cell, pair range) items,
+ * finalisation) is captured into a CUDA graph on the first call for a given (f, Q) pair and
+ * replayed afterwards (pg_boltz_batched_use_graph(plan, 0) launches directly instead).
+ */
+int pg_boltz_collide_batched(pg_boltz_plan_t *plan, const double *f_packed_dev, double *Q_packed_dev);
+
+/* Offsets (in doubles) of each cell in the packed arrays: offsets_host[0..ncell], last = total. */
+int pg_boltz_batched_offsets(const pg_boltz_plan_t *plan, long long *offsets_host);
+
+/* 1 (default): replay a captured CUDA graph in pg_boltz_collide_batched; 0: direct launches. */
+int pg_boltz_batched_use_graph(pg_boltz_plan_t *plan, int enable);
+
+/*
+ * Measured throughput (atomic additions per second, whole GPU) of 32-bit integer atomic adds
+ * to shared memory at random addresses of a 16,900-cell tile -- the operation that bounds
+ * the spreading kernels.  No counterpart in the paper; used as the measured roofline of
+ * spreading.  Allocates and frees 64 bytes; synchronises cuda_stream.  PG_OK / PG_ERR_CUDA.
+ */
+int pg_boltz_probe_shared_atomics(void *cuda_stream, double *rate_out);
 
 /*
  * Size of the library-owned static device array used by pg_boltz_project_noalloc

@@ -23,7 +23,9 @@ EXPORTS = (
     "pg_boltz_plan", "pg_boltz_plan_ex", "pg_boltz_set_stream", "pg_boltz_collide",
     "pg_boltz_moments", "pg_boltz_project_nodes", "pg_boltz_project", "pg_boltz_info",
     "pg_boltz_destroy", "pg_boltz_last_error", "pg_boltz_debug_fail_alloc", "pg_boltz_set_timing",
-    "pg_boltz_stage_times", "pg_boltz_project_noalloc",
+    "pg_boltz_stage_times", "pg_boltz_project_noalloc", "pg_boltz_probe_shared_atomics",
+    "pg_boltz_plan_batched", "pg_boltz_plan_batched_ex", "pg_boltz_collide_batched", "pg_boltz_batched_offsets",
+    "pg_boltz_batched_use_graph",
 )
 
 
@@ -85,6 +87,19 @@ def lib():
     L.pg_boltz_last_error.restype = ctypes.c_char_p
     L.pg_boltz_debug_fail_alloc.argtypes = [ctypes.c_int]
     L.pg_boltz_debug_fail_alloc.restype = None
+    ip_ = ctypes.POINTER(ctypes.c_int)
+    L.pg_boltz_plan_batched.argtypes = [ctypes.c_int, ctypes.c_int, ip_, ip_, dp, dp, ctypes.c_double]
+    L.pg_boltz_plan_batched.restype = vp
+    L.pg_boltz_plan_batched_ex.argtypes = [ctypes.POINTER(Opts), ctypes.c_int, ip_, ip_, dp, dp]
+    L.pg_boltz_plan_batched_ex.restype = vp
+    L.pg_boltz_collide_batched.argtypes = [vp, vp, vp]
+    L.pg_boltz_collide_batched.restype = ctypes.c_int
+    L.pg_boltz_batched_offsets.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.pg_boltz_batched_offsets.restype = ctypes.c_int
+    L.pg_boltz_batched_use_graph.argtypes = [vp, ctypes.c_int]
+    L.pg_boltz_batched_use_graph.restype = ctypes.c_int
+    L.pg_boltz_probe_shared_atomics.argtypes = [vp, dp]
+    L.pg_boltz_probe_shared_atomics.restype = ctypes.c_int
     L.pg_boltz_set_timing.argtypes = [vp, ctypes.c_int]
     L.pg_boltz_stage_times.argtypes = [vp, dp]
     for name in ("pg_boltz_set_timing", "pg_boltz_stage_times", "pg_boltz_set_stream", "pg_boltz_collide", "pg_boltz_moments", "pg_boltz_project_nodes",
@@ -109,6 +124,14 @@ def _ptr(x):
     if not x.is_cuda or not x.is_contiguous() or str(x.dtype) != "torch.float64":
         raise ValueError("expected a contiguous float64 CUDA tensor")
     return x.data_ptr()
+
+
+def probe_shared_atomics(stream=None) -> float:
+    """Measured int32 shared-memory atomic adds per second of the current GPU."""
+    out = ctypes.c_double(0.0)
+    raw = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(lib().pg_boltz_probe_shared_atomics(ctypes.c_void_p(raw), ctypes.byref(out)))
+    return out.value
 
 
 class Plan:
@@ -186,3 +209,34 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class BatchedPlan(Plan):
+    """Many independent operators (pg_boltz_plan_batched_ex) evaluated by one call."""
+
+    def __init__(self, d, N, M, S, kernel_gamma, tol, *, map_log=False, precision=PG_PREC_AUTO,
+                 sphere=PG_SPHERE_AUTO, upsampfac=0.0, spread_threads=0, spread_blocks_per_sm=0,
+                 screen=False):
+        n = len(N)
+        arr_i = ctypes.c_int * n
+        arr_d = ctypes.c_double * n
+        o = Opts(d=d, N=0, M=0, S=0.0, kernel_gamma=0.0, tol=tol, map_log=int(map_log), precision=precision,
+                 sphere=sphere, upsampfac=upsampfac, proj_nodes=0, spread_threads=spread_threads,
+                 spread_blocks_per_sm=spread_blocks_per_sm, screen=int(screen))
+        h = lib().pg_boltz_plan_batched_ex(ctypes.byref(o), n, arr_i(*[int(x) for x in N]),
+                                           arr_i(*[int(x) for x in M]), arr_d(*[float(x) for x in S]),
+                                           arr_d(*[float(x) for x in kernel_gamma]))
+        if not h:
+            raise PGBoltzError(PG_ERR_ARG, last_error())
+        self._h = ctypes.c_void_p(h)
+        self.d, self.ncell = d, n
+        off = (ctypes.c_longlong * (n + 1))()
+        _check(lib().pg_boltz_batched_offsets(self._h, off))
+        self.offsets = list(off)
+        self.n_modes = self.offsets[-1]
+
+    def collide(self, f, Q):
+        _check(lib().pg_boltz_collide_batched(self._h, ctypes.c_void_p(_ptr(f)), ctypes.c_void_p(_ptr(Q))))
+
+    def use_graph(self, enable: bool):
+        _check(lib().pg_boltz_batched_use_graph(self._h, int(bool(enable))))

@@ -1,0 +1,896 @@
+// Batched evaluation of many independent collision operators (one velocity distribution
+// per spatial cell of an inhomogeneous solver), each with its own N, M, S and gamma, in
+// three launches replayed as a CUDA graph:
+//   1. k_batch_prep   (one block per cell): reconstruction of f_N at the interior CGL nodes,
+//      loss weights h_i (Eq. Qminus) and the strength bound B_c of the cell;
+//   2. k_batch_spread (persistent, one or more blocks per SM): work items (cell, range of
+//      node pairs) are taken from a global counter; a block keeps the folded grid of its
+//      current cell in shared memory and adds it to the cell's global fixed-point grid when
+//      it moves to another cell;
+//   3. k_batch_final  (one block per cell): cosine transform + deconvolution of the cell's
+//      grid, forward Chebyshev transform of the loss, Q = Q+ - Q-.
+// The per-point arithmetic is the same as the single-plan path (spread_impl.cuh).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "host.cuh"
+#include "spread_impl.cuh"
+
+#define PG_API extern "C" __attribute__((visibility("default")))
+
+using namespace pgbh;
+
+namespace pgb {
+
+struct CellDesc {
+    int N, M, nf, n, nnode, fast_gamma;
+    double S, gamma, Wsig;
+    long long pairs;     // nnode^2
+    long long f_off;     // packed modes (f~ and Q)
+    long long a_off;     // packed node values (a, h)
+    long long grid_off;  // packed folded grids
+    long long s_off;     // packed scratch: four buffers of s_len doubles
+    long long s_len;
+    int node_off;        // node tables (v, scale_a, inv_mu2)
+    int R_off;           // R (N x (N+1)) and E ((N+1) x N)
+    int D_off;           // D ((N+1) x nf)
+    int sig_off;         // sphere points (M x d) and weights (M)
+    int chunk;           // node pairs per work item
+    int item0;           // first work item of the cell
+};
+
+struct BatchArgs {
+    int d, r, ncell, nitems, w;
+    double Bconst, beta, screen_eps;
+    const CellDesc *cells;
+    const int *item_cell;
+    int *counter;
+    const double *f;
+    double *Q;
+    double *a64;
+    float *a32;
+    double *h;
+    double *Bcell;
+    double *Tcell;  // per-cell screening threshold (0: spread every pair)
+    unsigned long long *grid;
+    double *scratch;
+    const double *v64;
+    const float *v32;
+    const double *scale_a;
+    const double *inv_mu2;
+    const double *R;
+    const double *E;
+    const double *D;
+    const double *sig64;
+    const float *sig32;
+    const double *wsig64;
+    const float *wsig32;
+};
+
+namespace {
+
+constexpr int kPrepThreads = 256;
+
+__device__ __forceinline__ Dims3 dims3(int d, int a, int b, int c)
+{
+    Dims3 x;
+    x.e[0] = (d == 2) ? 1 : a;
+    x.e[1] = b;
+    x.e[2] = c;
+    return x;
+}
+
+// out = A contracted with `in` along axis ax, by the whole block.
+__device__ void block_pass(const double *in, Dims3 id, int ax, const double *A, int m, double *out)
+{
+    Dims3 od = id;
+    od.e[ax] = m;
+    const int total = od.e[0] * od.e[1] * od.e[2];
+    const int len = id.e[ax];
+    const int sax = (ax == 2) ? 1 : (ax == 1 ? id.e[2] : id.e[1] * id.e[2]);
+    for (int o = threadIdx.x; o < total; o += blockDim.x) {
+        int oc[3];
+        oc[2] = o % od.e[2];
+        const int t = o / od.e[2];
+        oc[1] = t % od.e[1];
+        oc[0] = t / od.e[1];
+        const int k = oc[ax];
+        oc[ax] = 0;
+        const int base = (oc[0] * id.e[1] + oc[1]) * id.e[2] + oc[2];
+        double acc = 0.0;
+        for (int s = 0; s < len; ++s) acc = fma(A[k * len + s], in[base + s * sax], acc);
+        out[o] = acc;
+    }
+}
+
+__device__ void block_pass_fixed(const unsigned long long *in, Dims3 id, int ax, const double *A, int m,
+                                 double unit, double *out)
+{
+    Dims3 od = id;
+    od.e[ax] = m;
+    const int total = od.e[0] * od.e[1] * od.e[2];
+    const int len = id.e[ax];
+    const int sax = (ax == 2) ? 1 : (ax == 1 ? id.e[2] : id.e[1] * id.e[2]);
+    for (int o = threadIdx.x; o < total; o += blockDim.x) {
+        int oc[3];
+        oc[2] = o % od.e[2];
+        const int t = o / od.e[2];
+        oc[1] = t % od.e[1];
+        oc[0] = t / od.e[1];
+        const int k = oc[ax];
+        oc[ax] = 0;
+        const int base = (oc[0] * id.e[1] + oc[1]) * id.e[2] + oc[2];
+        double acc = 0.0;
+        for (int s = 0; s < len; ++s) acc = fma(A[k * len + s], (double)(long long)in[base + s * sax], acc);
+        out[o] = acc * unit;
+    }
+}
+
+__device__ double block_reduce_sum(double v, double *warp_part)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) warp_part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += warp_part[w];  // fixed order
+    __syncthreads();
+    return s;
+}
+
+// One block per cell: a_i, h_i and the strength bound B_c (same formulas as k_recon_last,
+// k_loss and k_bound_reduce of the single-plan path).  PT is the arithmetic of the pair
+// distances and |v_i - v_j|^gamma (float for FP32 plans; sums are FP64 either way).
+template <typename PT>
+__global__ void __launch_bounds__(kPrepThreads) k_batch_prep(const __grid_constant__ BatchArgs b)
+{
+    __shared__ double warp_part[kPrepThreads / 32];
+    __shared__ unsigned s_hist[kScreenBins];
+    const bool screen = b.screen_eps > 0.0;
+    for (int k = threadIdx.x; k < kScreenBins; k += blockDim.x) s_hist[k] = 0u;
+    const int c = blockIdx.x;
+    const CellDesc cd = b.cells[c];
+    const int d = b.d, N = cd.N, nnode = cd.nnode;
+    double *s1 = b.scratch + cd.s_off, *s2 = s1 + cd.s_len;
+    const double *R = b.R + cd.R_off;
+    // 1. reconstruction: leading passes, then the last axis with a_i = W_i mu_i^2 P_i
+    Dims3 dims = dims3(d, N + 1, N + 1, N + 1);
+    const double *cur = b.f + cd.f_off;
+    double *bufs[2] = {s1, s2};
+    int which = 0;
+    for (int ax = 3 - d; ax < 2; ++ax) {
+        block_pass(cur, dims, ax, R, N, bufs[which]);
+        __syncthreads();
+        dims.e[ax] = N;
+        cur = bufs[which];
+        which ^= 1;
+    }
+    const double *sa = b.scale_a + cd.node_off;
+    double *a = b.a64 + cd.a_off;
+    float *af = b.a32 + cd.a_off;
+    for (int o = threadIdx.x; o < nnode; o += blockDim.x) {
+        const int o2 = o % N, t = o / N, o1 = t % dims.e[1], o0 = t / dims.e[1];
+        const double *src = cur + (o0 * dims.e[1] + o1) * (N + 1);
+        double acc = 0.0;
+        for (int s = 0; s <= N; ++s) acc = fma(R[o2 * (N + 1) + s], src[s], acc);
+        double scl = sa[o1] * sa[o2];
+        if (d == 3) scl *= sa[o0];
+        a[o] = acc * scl;
+        af[o] = (float)(acc * scl);
+    }
+    __syncthreads();
+    // 2. loss sums and the strength bound
+    const PT *vn = nullptr;
+    if constexpr (sizeof(PT) == 4) vn = b.v32 + cd.node_off;
+    else vn = b.v64 + cd.node_off;
+    const double *im = b.inv_mu2 + cd.node_off;
+    const double Bw = b.Bconst * cd.Wsig;
+    const PT S = PT(cd.S), invS = PT(1) / S, gam = PT(cd.gamma);
+    double bsum = 0.0;
+    for (int i = threadIdx.x; i < nnode; i += blockDim.x) {
+        int idx[3] = {0, 0, 0}, t = i;
+        for (int l = d - 1; l >= 0; --l) {
+            idx[l] = t % N;
+            t /= N;
+        }
+        PT vi[3];
+        for (int l = 0; l < 3; ++l) vi[l] = (l < d) ? vn[idx[l]] : PT(0);
+        double L = 0.0, U = 0.0;
+        for (int j0 = 0; j0 < nnode; j0 += 64) {
+            PT Lp = PT(0), Up = PT(0);  // partial sums of 64 terms, then FP64
+            const int j1 = min(j0 + 64, nnode);
+            for (int j = j0; j < j1; ++j) {
+                int u = j;
+                PT g2 = PT(0), mu = PT(1);
+                PT vj[3];
+                for (int l = d - 1; l >= 0; --l) {
+                    vj[l] = vn[u % N];
+                    u /= N;
+                    const PT dl = vi[l] - vj[l];
+                    g2 += dl * dl;
+                }
+                const PT g = sqrt(g2);
+                PT B;
+                switch (cd.fast_gamma) {
+                case 0: B = PT(1); break;
+                case 1: B = g; break;
+                case 2: B = sqrt(g); break;
+                default: B = (g2 > PT(0)) ? pow(g, gam) : PT(0); break;
+                }
+                const PT aj = PT(a[j]);
+                Lp += aj * B;
+                for (int l = 0; l < d; ++l) {
+                    const PT R_ = fabs(PT(0.5) * (vi[l] + vj[l])) + PT(0.5) * g;
+                    mu *= (b.r == 1) ? (S * S + R_ * R_) * invS : S * cosh(R_ * invS);
+                }
+                const PT pb = fabs(aj) * B * mu;
+                Up += pb;
+                if (screen && pb > PT(0)) atomicAdd(&s_hist[screen_bin(fabs(a[i]) * Bw * (double)pb)], 1u);
+            }
+            L += (double)Lp;
+            U += (double)Up;
+        }
+        double scl = 1.0;
+        for (int l = 0; l < d; ++l) scl *= im[idx[l]];
+        b.h[cd.a_off + i] = a[i] * Bw * L * scl;
+        bsum += fabs(a[i]) * Bw * U;
+    }
+    const double tot = block_reduce_sum(bsum, warp_part);
+    if (threadIdx.x == 0) {
+        const double Bv = tot * (1.0 + 1e-5);  // margin for the FP32 partial sums
+        b.Bcell[c] = Bv;
+        // screening threshold of the cell: same rule as k_bound_reduce of the single-plan path
+        double t = 0.0;
+        if (screen && Bv > 0.0) {
+            double cum = 0.0;
+            int k = 0;
+            for (; k < kScreenBins - 1; ++k) {
+                const double add = (double)s_hist[k] * ldexp(1.0, k + 1 - kScreenOffset);
+                if (cum + add > b.screen_eps * Bv) break;
+                cum += add;
+            }
+            t = ldexp(1.0, k - kScreenOffset);
+        }
+        b.Tcell[c] = t;
+    }
+}
+
+// Spreading arguments of one cell for the shared per-point code.
+__device__ __forceinline__ void cell_args(const BatchArgs &b, const CellDesc &cd, bool f32, SpreadArgs &sa)
+{
+    sa.d = b.d;
+    sa.N = cd.N;
+    sa.M = cd.M;
+    sa.r = b.r;
+    sa.nnode = cd.nnode;
+    sa.npairs = cd.pairs;
+    sa.n = cd.n;
+    sa.nf = cd.nf;
+    sa.rows_per_slab = cd.nf;
+    sa.nslab = 1;
+    sa.fast_gamma = cd.fast_gamma;
+    sa.S = cd.S;
+    sa.gamma = cd.gamma;
+    sa.Bconst = b.Bconst;
+    sa.beta = b.beta;
+    sa.grid_scale = cd.n / (2.0 * 3.14159265358979323846);
+    sa.vnode = f32 ? (const void *)(b.v32 + cd.node_off) : (const void *)(b.v64 + cd.node_off);
+    sa.a = f32 ? (const void *)(b.a32 + cd.a_off) : (const void *)(b.a64 + cd.a_off);
+    sa.sig = f32 ? (const void *)(b.sig32 + cd.sig_off * b.d) : (const void *)(b.sig64 + cd.sig_off * b.d);
+    sa.wsig = f32 ? (const void *)(b.wsig32 + cd.sig_off) : (const void *)(b.wsig64 + cd.sig_off);
+    sa.Wsig = cd.Wsig;
+    sa.bound = nullptr;
+    sa.tau = nullptr;  // the batched kernel reads Tcell directly
+    sa.grid = b.grid + cd.grid_off;
+    sa.simple_fold = (b.w <= cd.n / 2) ? 1 : 0;
+}
+
+template <typename T>
+constexpr int max_threads_of() { return sizeof(T) == 4 ? kMaxThreadsF32 : kMaxThreadsF64; }
+
+template <typename T, int D, int W>
+__global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __grid_constant__ BatchArgs b)
+{
+    using namespace spread_detail;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
+    __shared__ CellDesc s_cd;
+    constexpr bool F32 = (sizeof(T) == 4);
+    int cur = -1, ncell = 0, plane = 0, Eg = 0, shift = 0;
+    T sc = T(0), tau = T(0);
+    SpreadArgs sa;
+    unsigned *lo = reinterpret_cast<unsigned *>(smem_raw);
+    int *hi = nullptr;
+    double *dv = reinterpret_cast<double *>(smem_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(b.counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= b.nitems) break;  // uniform over the block
+        const int cell = b.item_cell[item];
+        if (cell != cur) {
+            if (cur >= 0) {
+                // add the previous cell's tile to its grid
+                unsigned long long *g = sa.grid;
+                for (int e = threadIdx.x; e < ncell; e += blockDim.x) {
+                    if constexpr (F32) {
+                        const long long v = (long long)(((unsigned long long)(unsigned)hi[e] << 32) | lo[e]);
+                        if (v && shift <= 62) atomicAdd(g + e, (unsigned long long)(v * (1ll << shift)));
+                    } else {
+                        const long long v = __double2ll_rn(dv[e] * ldexp(1.0, Eg));
+                        if (v) atomicAdd(g + e, (unsigned long long)v);
+                    }
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) s_cd = b.cells[cell];
+            __syncthreads();
+            cur = cell;
+            cell_args(b, s_cd, F32, sa);
+            plane = (D == 3) ? s_cd.nf * s_cd.nf : s_cd.nf;
+            ncell = plane * s_cd.nf;
+            hi = reinterpret_cast<int *>(smem_raw) + ncell;
+            const double Bc = b.Bcell[cell];
+            Eg = global_exponent(Bc);
+            const int Et = F32 ? min(Eg - 10, 120) : Eg;
+            shift = Eg - Et;
+            sc = F32 ? T(ldexp(1.0, Et)) : T(1);
+            tau = T(b.Tcell[cell]);
+            for (int e = threadIdx.x; e < ncell; e += blockDim.x) {
+                if constexpr (F32) {
+                    lo[e] = 0u;
+                    hi[e] = 0;
+                } else {
+                    dv[e] = 0.0;
+                }
+            }
+            __syncthreads();
+        }
+        // the item's node pairs; lanes of a warp take pairs nwarp apart
+        const long long p0 = (long long)(item - s_cd.item0) * s_cd.chunk;
+        const long long p1 = min(p0 + (long long)s_cd.chunk, s_cd.pairs);
+        for (long long pr = p0 + (long long)lane * nwarp + warp; pr < p1; pr += blockDim.x) {
+            PairData<T, D> P;
+            if (!load_pair<T, D>(sa, pr, P)) continue;
+            if (tau > T(0) && pair_bound<T, D>(sa, P) < tau) continue;
+            if constexpr (F32) {
+                spread_pair<T, D, W>(sa, P, sc, SplitTile{lo, hi}, 0, s_cd.nf, plane);
+            } else {
+                spread_pair<T, D, W>(sa, P, sc, DoubleTile{dv}, 0, s_cd.nf, plane);
+            }
+        }
+        __syncthreads();
+    }
+    if (cur >= 0) {
+        unsigned long long *g = sa.grid;
+        for (int e = threadIdx.x; e < ncell; e += blockDim.x) {
+            if constexpr (F32) {
+                const long long v = (long long)(((unsigned long long)(unsigned)hi[e] << 32) | lo[e]);
+                if (v && shift <= 62) atomicAdd(g + e, (unsigned long long)(v * (1ll << shift)));
+            } else {
+                const long long v = __double2ll_rn(dv[e] * ldexp(1.0, Eg));
+                if (v) atomicAdd(g + e, (unsigned long long)v);
+            }
+        }
+    }
+}
+
+// One block per cell: Q = D(grid) - E(h) along every axis (Section 4.2).
+__global__ void __launch_bounds__(kPrepThreads) k_batch_final(const __grid_constant__ BatchArgs b)
+{
+    const int c = blockIdx.x;
+    const CellDesc cd = b.cells[c];
+    const int d = b.d, N = cd.N, nf = cd.nf;
+    double *s1 = b.scratch + cd.s_off, *s2 = s1 + cd.s_len, *s3 = s2 + cd.s_len, *s4 = s3 + cd.s_len;
+    const double *Dm = b.D + cd.D_off;
+    const double *E = b.E + cd.R_off;
+    const double unit = ldexp(1.0, -global_exponent(b.Bcell[c]));
+    Dims3 gd = dims3(d, nf, nf, nf);
+    const int ax0 = 3 - d;
+    block_pass_fixed(b.grid + cd.grid_off, gd, ax0, Dm, N + 1, unit, s1);
+    __syncthreads();
+    gd.e[ax0] = N + 1;
+    const double *gcur = s1;
+    if (d == 3) {
+        block_pass(s1, gd, 1, Dm, N + 1, s2);
+        __syncthreads();
+        gd.e[1] = N + 1;
+        gcur = s2;
+    }
+    Dims3 hd = dims3(d, N, N, N);
+    const double *hcur = b.h + cd.a_off;
+    double *hb[2] = {s3, s4};
+    int which = 0;
+    for (int ax = 3 - d; ax < 2; ++ax) {
+        block_pass(hcur, hd, ax, E, N + 1, hb[which]);
+        __syncthreads();
+        hd.e[ax] = N + 1;
+        hcur = hb[which];
+        which ^= 1;
+    }
+    const int total = gd.e[0] * gd.e[1] * (N + 1);
+    double *Q = b.Q + cd.f_off;
+    for (int o = threadIdx.x; o < total; o += blockDim.x) {
+        const int o2 = o % (N + 1), row = o / (N + 1);
+        const double *gs = gcur + row * nf;
+        const double *hs = hcur + row * N;
+        double qp = 0.0, qm = 0.0;
+        for (int s = 0; s < nf; ++s) qp = fma(Dm[o2 * nf + s], gs[s], qp);
+        for (int s = 0; s < N; ++s) qm = fma(E[o2 * N + s], hs[s], qm);
+        Q[o] = qp - qm;
+    }
+}
+
+template <typename T, int D, int W>
+cudaError_t set_spread_attr(size_t smem)
+{
+    return cudaFuncSetAttribute(k_batch_spread<T, D, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <typename T, int D, int W, int WMAX>
+struct BatchDispatch {
+    static cudaError_t attr(int w, size_t smem)
+    {
+        if (w == W) return set_spread_attr<T, D, W>(smem);
+        return BatchDispatch<T, D, W + 1, WMAX>::attr(w, smem);
+    }
+    static cudaError_t launch(int w, const BatchArgs &b, int blocks, int threads, size_t smem, cudaStream_t s)
+    {
+        if (w == W) {
+            k_batch_spread<T, D, W><<<blocks, threads, smem, s>>>(b);
+            return cudaGetLastError();
+        }
+        return BatchDispatch<T, D, W + 1, WMAX>::launch(w, b, blocks, threads, smem, s);
+    }
+};
+template <typename T, int D, int WMAX>
+struct BatchDispatch<T, D, WMAX, WMAX> {
+    static cudaError_t attr(int w, size_t smem)
+    {
+        return (w == WMAX) ? set_spread_attr<T, D, WMAX>(smem) : cudaErrorInvalidValue;
+    }
+    static cudaError_t launch(int w, const BatchArgs &b, int blocks, int threads, size_t smem, cudaStream_t s)
+    {
+        if (w != WMAX) return cudaErrorInvalidValue;
+        k_batch_spread<T, D, WMAX><<<blocks, threads, smem, s>>>(b);
+        return cudaGetLastError();
+    }
+};
+
+// The batched spreading kernels cover the widths the FP32 path uses (w <= 10) in FP32 and
+// the FP64 widths up to 16.
+cudaError_t batch_spread_attr(bool f32, int d, int w, size_t smem)
+{
+    if (f32) return d == 2 ? BatchDispatch<float, 2, kMinWidth, kMaxWidthF32>::attr(w, smem)
+                           : BatchDispatch<float, 3, kMinWidth, kMaxWidthF32>::attr(w, smem);
+    return d == 2 ? BatchDispatch<double, 2, kMinWidth, kMaxWidthF64>::attr(w, smem)
+                  : BatchDispatch<double, 3, kMinWidth, kMaxWidthF64>::attr(w, smem);
+}
+
+cudaError_t batch_spread_launch(bool f32, int d, int w, const BatchArgs &b, int blocks, int threads, size_t smem,
+                                cudaStream_t s)
+{
+    if (f32) return d == 2 ? BatchDispatch<float, 2, kMinWidth, kMaxWidthF32>::launch(w, b, blocks, threads, smem, s)
+                           : BatchDispatch<float, 3, kMinWidth, kMaxWidthF32>::launch(w, b, blocks, threads, smem, s);
+    return d == 2 ? BatchDispatch<double, 2, kMinWidth, kMaxWidthF64>::launch(w, b, blocks, threads, smem, s)
+                  : BatchDispatch<double, 3, kMinWidth, kMaxWidthF64>::launch(w, b, blocks, threads, smem, s);
+}
+
+}  // namespace
+}  // namespace pgb
+
+// ============================================================================ host
+
+struct BatchState {
+    int d = 2, ncell = 0, r = 1, prec = PG_PREC_FP32, w = 0;
+    double tol = 1e-6, sigma = 2.0, beta = 0.0;
+    std::vector<long long> offsets;  // ncell + 1 packed mode offsets
+    long long points = 0, pairs = 0, grid_cells = 0;
+    int nitems = 0;
+    int spread_blocks = 0, spread_threads = 0;
+    size_t spread_smem = 0;
+    pgb::BatchArgs args{};
+    bool use_graph = true;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const double *g_f = nullptr;
+    double *g_Q = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    bool timing = false, timed = false;
+};
+
+void pg_free_batch(BatchState *b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (cudaEvent_t e : b->ev)
+        if (e) cudaEventDestroy(e);
+    delete b;
+}
+
+namespace {
+
+constexpr long long kItemPoints = 1 << 17;  // points per work item
+
+int enqueue_batch(pg_boltz_plan_t *p, cudaStream_t s, const double *f, double *Q)
+{
+    BatchState &B = *p->batch;
+    pgb::BatchArgs a = B.args;
+    a.f = f;
+    a.Q = Q;
+    int rc;
+    // the work counter and the grids share one allocation: [counter | 256-byte gap | grids]
+    if ((rc = cuda_check(cudaMemsetAsync(a.counter, 0, 256 + (size_t)B.grid_cells * 8, s), "memset grids")))
+        return rc;
+    const bool f32 = (B.prec == PG_PREC_FP32);
+    if (f32) pgb::k_batch_prep<float><<<B.ncell, pgb::kPrepThreads, 0, s>>>(a);
+    else pgb::k_batch_prep<double><<<B.ncell, pgb::kPrepThreads, 0, s>>>(a);
+    if ((rc = cuda_check(cudaGetLastError(), "batched prep"))) return rc;
+    if ((rc = cuda_check(pgb::batch_spread_launch(f32, B.d, B.w, a, B.spread_blocks, B.spread_threads, B.spread_smem, s),
+                         "batched spread")))
+        return rc;
+    pgb::k_batch_final<<<B.ncell, pgb::kPrepThreads, 0, s>>>(a);
+    return cuda_check(cudaGetLastError(), "batched final");
+}
+
+}  // namespace
+
+PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, int ncell, const int *Ns, const int *Ms,
+                                                 const double *Ss, const double *gammas)
+{
+    if (!opts || !Ns || !Ms || !Ss || !gammas || ncell < 1) {
+        set_error(PG_ERR_ARG, "batched plan: NULL array or ncell < 1");
+        return nullptr;
+    }
+    const pg_boltz_opts_t &o = *opts;
+    if (o.d != 2 && o.d != 3) {
+        set_error(PG_ERR_ARG, "d must be 2 or 3 (got %d)", o.d);
+        return nullptr;
+    }
+    if (!(o.tol >= 1e-15 && o.tol <= 1e-2)) {
+        set_error(PG_ERR_ARG, "tol must be in [1e-15, 1e-2] (got %g)", o.tol);
+        return nullptr;
+    }
+    if (o.upsampfac != 0.0 && !(o.upsampfac >= 1.5 && o.upsampfac <= 4.0)) {
+        set_error(PG_ERR_ARG, "upsampfac must be in [1.5, 4] (got %g)", o.upsampfac);
+        return nullptr;
+    }
+    for (int c = 0; c < ncell; ++c) {
+        if (Ns[c] < 2 || Ns[c] > (o.d == 2 ? 200 : 40) || Ms[c] < 2 || Ms[c] % 2 || !(Ss[c] > 0.0) ||
+            !(gammas[c] >= 0.0 && gammas[c] <= 1.0)) {
+            set_error(PG_ERR_ARG, "cell %d: need 2 <= N <= %d, even M >= 2, S > 0, 0 <= gamma <= 1", c,
+                      o.d == 2 ? 200 : 40);
+            return nullptr;
+        }
+    }
+    pg_boltz_plan_t *p = new (std::nothrow) pg_boltz_plan_t();
+    BatchState *B = p ? new (std::nothrow) BatchState() : nullptr;
+    if (!p || !B) {
+        delete p;
+        set_error(PG_ERR_NOMEM, "host allocation failed");
+        return nullptr;
+    }
+    p->batch = B;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        cudaGetLastError();
+        set_error(PG_ERR_CUDA, "no CUDA device available");
+        free_plan(p);
+        return nullptr;
+    }
+    const int d = o.d;
+    B->d = d;
+    B->ncell = ncell;
+    B->r = o.map_log ? 0 : 1;
+    B->tol = o.tol;
+    B->prec = (o.precision == PG_PREC_AUTO) ? (o.tol < 1e-8 ? PG_PREC_FP64 : PG_PREC_FP32) : o.precision;
+    B->sigma = (o.upsampfac > 0.0) ? o.upsampfac : 2.0;
+    B->w = width_for(o.tol, B->sigma);
+    const bool f32 = (B->prec == PG_PREC_FP32);
+    const int wmax = f32 ? pgb::kMaxWidthF32 : pgb::kMaxWidthF64;
+    if (B->w > wmax) {
+        if (f32) B->w = wmax;
+        else {
+            set_error(PG_ERR_ARG, "tol %g needs kernel width %d > %d", o.tol, B->w, wmax);
+            free_plan(p);
+            return nullptr;
+        }
+    }
+    B->beta = kernel_beta(B->w, B->sigma);
+    const int sphere = (d == 3) ? (o.sphere == PG_SPHERE_AUTO ? PG_SPHERE_ANTIPODAL : o.sphere) : PG_SPHERE_AUTO;
+
+    // ---- tables, shared between cells with equal parameters
+    std::vector<double> v64, scale_a, inv_mu2, R, E, D, sig64, wsig64;
+    std::map<std::pair<int, double>, int> node_key;
+    std::map<int, std::pair<int, int>> mat_key;  // N -> (R_off, D_off)
+    std::map<int, int> sig_key;
+    std::vector<pgb::CellDesc> cells(ncell);
+    std::vector<int> item_cell;
+    long long f_off = 0, a_off = 0, grid_off = 0, s_off = 0;
+    int max_cells_tile = 0;
+    B->offsets.assign(ncell + 1, 0);
+    for (int c = 0; c < ncell; ++c) {
+        pgb::CellDesc &cd = cells[c];
+        const int N = Ns[c], M = Ms[c];
+        cd.N = N;
+        cd.M = M;
+        cd.n = grid_size(N, B->sigma);
+        cd.nf = cd.n / 2 + 1;
+        cd.nnode = (d == 2) ? N * N : N * N * N;
+        cd.fast_gamma = (gammas[c] == 0.0) ? 0 : (gammas[c] == 1.0) ? 1 : (gammas[c] == 0.5) ? 2 : 3;
+        cd.S = Ss[c];
+        cd.gamma = gammas[c];
+        cd.pairs = (long long)cd.nnode * cd.nnode;
+        auto nk = std::make_pair(N, Ss[c]);
+        if (!node_key.count(nk)) {
+            NodeTables nt = node_tables(N, Ss[c], B->r);
+            node_key[nk] = (int)v64.size();
+            v64.insert(v64.end(), nt.v.begin(), nt.v.end());
+            scale_a.insert(scale_a.end(), nt.scale_a.begin(), nt.scale_a.end());
+            inv_mu2.insert(inv_mu2.end(), nt.inv_mu2.begin(), nt.inv_mu2.end());
+        }
+        cd.node_off = node_key[nk];
+        if (!mat_key.count(N)) {
+            NodeTables nt = node_tables(N, 1.0, B->r);  // R and E do not depend on S
+            std::vector<double> Dm = transform_matrix(N, cd.n, B->w, B->beta);
+            mat_key[N] = std::make_pair((int)R.size(), (int)D.size());
+            R.insert(R.end(), nt.R.begin(), nt.R.end());
+            E.insert(E.end(), nt.E.begin(), nt.E.end());
+            D.insert(D.end(), Dm.begin(), Dm.end());
+        }
+        cd.R_off = mat_key[N].first;
+        cd.D_off = mat_key[N].second;
+        if (!sig_key.count(M)) {
+            std::vector<double> sp, sw;
+            sphere_points(d, M, sphere, sp, sw);
+            sig_key[M] = (int)wsig64.size();
+            sig64.insert(sig64.end(), sp.begin(), sp.end());
+            wsig64.insert(wsig64.end(), sw.begin(), sw.end());
+        }
+        cd.sig_off = sig_key[M];
+        cd.Wsig = 0.0;
+        for (int m = 0; m < M; ++m) cd.Wsig += wsig64[cd.sig_off + m];
+        const long long modes = (long long)ipow(N + 1, d);
+        cd.f_off = f_off;
+        B->offsets[c] = f_off;
+        f_off += modes;
+        cd.a_off = a_off;
+        a_off += cd.nnode;
+        const long long cells_tile = (long long)ipow(cd.nf, d);
+        cd.grid_off = grid_off;
+        grid_off += cells_tile;
+        max_cells_tile = std::max<int>(max_cells_tile, (int)cells_tile);
+        cd.s_len = std::max<long long>(modes, (long long)(N + 1) * (long long)ipow(cd.nf, d - 1));
+        cd.s_off = s_off;
+        s_off += 4 * cd.s_len;
+        cd.chunk = (int)std::max<long long>(64, kItemPoints / M);
+        cd.item0 = (int)item_cell.size();
+        const long long nitem = (cd.pairs + cd.chunk - 1) / cd.chunk;
+        for (long long t = 0; t < nitem; ++t) item_cell.push_back(c);
+        B->points += cd.pairs * M;
+        B->pairs += cd.pairs;
+    }
+    B->offsets[ncell] = f_off;
+    B->nitems = (int)item_cell.size();
+    B->grid_cells = grid_off;
+    std::vector<float> v32(v64.begin(), v64.end()), sig32(sig64.begin(), sig64.end()), wsig32(wsig64.begin(), wsig64.end());
+
+    pgb::BatchArgs &a = B->args;
+    a.d = d;
+    a.r = B->r;
+    a.ncell = ncell;
+    a.nitems = B->nitems;
+    a.w = B->w;
+    a.Bconst = 1.0 / (d == 2 ? 2.0 * kPi : 4.0 * kPi);
+    a.beta = B->beta;
+    a.screen_eps = o.screen ? 0.05 * o.tol : 0.0;
+    int rc;
+    pgb::CellDesc *d_cells = nullptr;
+    int *d_items = nullptr;
+    double *d_v64 = nullptr, *d_sa = nullptr, *d_im = nullptr, *d_R = nullptr, *d_E = nullptr, *d_D = nullptr,
+           *d_s64 = nullptr, *d_w64 = nullptr;
+    float *d_v32 = nullptr, *d_s32 = nullptr, *d_w32 = nullptr;
+    void *counter_grid = nullptr;
+    if ((rc = upload(p, &d_cells, cells)) || (rc = upload(p, &d_items, item_cell)) || (rc = upload(p, &d_v64, v64)) ||
+        (rc = upload(p, &d_v32, v32)) || (rc = upload(p, &d_sa, scale_a)) || (rc = upload(p, &d_im, inv_mu2)) ||
+        (rc = upload(p, &d_R, R)) || (rc = upload(p, &d_E, E)) || (rc = upload(p, &d_D, D)) ||
+        (rc = upload(p, &d_s64, sig64)) || (rc = upload(p, &d_s32, sig32)) || (rc = upload(p, &d_w64, wsig64)) ||
+        (rc = upload(p, &d_w32, wsig32)) || (rc = dev_alloc(p, (void **)&a.a64, a_off * 8)) ||
+        (rc = dev_alloc(p, (void **)&a.a32, a_off * 4)) || (rc = dev_alloc(p, (void **)&a.h, a_off * 8)) ||
+        (rc = dev_alloc(p, (void **)&a.Bcell, (size_t)ncell * 8)) ||
+        (rc = dev_alloc(p, (void **)&a.Tcell, (size_t)ncell * 8)) ||
+        (rc = dev_alloc(p, &counter_grid, 256 + (size_t)grid_off * 8)) ||
+        (rc = dev_alloc(p, (void **)&a.scratch, (size_t)s_off * 8))) {
+        free_plan(p);
+        return nullptr;
+    }
+    a.cells = d_cells;
+    a.item_cell = d_items;
+    a.counter = static_cast<int *>(counter_grid);
+    a.grid = reinterpret_cast<unsigned long long *>(static_cast<char *>(counter_grid) + 256);
+    a.v64 = d_v64;
+    a.v32 = d_v32;
+    a.scale_a = d_sa;
+    a.inv_mu2 = d_im;
+    a.R = d_R;
+    a.E = d_E;
+    a.D = d_D;
+    a.sig64 = d_s64;
+    a.sig32 = d_s32;
+    a.wsig64 = d_w64;
+    a.wsig32 = d_w32;
+
+    // ---- persistent spreading launch shape
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, p->device) != cudaSuccess) {
+        set_error(PG_ERR_CUDA, "cudaGetDeviceProperties failed");
+        free_plan(p);
+        return nullptr;
+    }
+    B->spread_smem = (size_t)max_cells_tile * 8;
+    if (B->spread_smem + 1024 > prop.sharedMemPerBlockOptin) {
+        set_error(PG_ERR_ARG, "largest cell's folded grid (%d cells) does not fit shared memory", max_cells_tile);
+        free_plan(p);
+        return nullptr;
+    }
+    const int max_threads = f32 ? pgb::kMaxThreadsF32 : pgb::kMaxThreadsF64;
+    int per_sm = (int)(prop.sharedMemPerMultiprocessor / (B->spread_smem + 2048 + prop.reservedSharedMemPerBlock));
+    per_sm = std::max(per_sm, 1);
+    if (o.spread_blocks_per_sm > 0) per_sm = std::min(per_sm, o.spread_blocks_per_sm);
+    B->spread_threads = (o.spread_threads > 0) ? o.spread_threads
+                                                : std::max(128, std::min(max_threads, (1024 / per_sm) / 32 * 32));
+    if (B->spread_threads % 32 || B->spread_threads > max_threads) {
+        set_error(PG_ERR_ARG, "spread_threads must be a multiple of 32 and <= %d", max_threads);
+        free_plan(p);
+        return nullptr;
+    }
+    per_sm = std::min(per_sm, std::max(1, prop.maxThreadsPerMultiProcessor / B->spread_threads));
+    B->spread_blocks = prop.multiProcessorCount * per_sm;
+    if ((rc = cuda_check(pgb::batch_spread_attr(f32, d, B->w, B->spread_smem), "batched spread attribute"))) {
+        free_plan(p);
+        return nullptr;
+    }
+    pg_boltz_info_t &in = p->info;
+    in.d = d;
+    in.N = Ns[0];
+    in.M = Ms[0];
+    in.r = B->r;
+    in.precision = B->prec;
+    in.sphere = sphere;
+    in.tol = o.tol;
+    in.upsampfac = B->sigma;
+    in.kernel_width = B->w;
+    in.kernel_beta = B->beta;
+    in.slabs = 1;
+    in.spread_blocks = B->spread_blocks;
+    in.spread_threads = B->spread_threads;
+    in.spread_smem_bytes = B->spread_smem;
+    in.points = B->points;
+    in.pairs = B->pairs;
+    in.launches_per_collide = 5;
+    in.device_bytes = p->device_bytes;
+    p->d = d;
+    p->prec = B->prec;
+    return p;
+}
+
+PG_API pg_boltz_plan_t *pg_boltz_plan_batched(int d, int ncell, const int *N, const int *M, const double *S,
+                                              const double *kernel_gamma, double tol)
+{
+    pg_boltz_opts_t o;
+    std::memset(&o, 0, sizeof(o));
+    o.d = d;
+    o.tol = tol;
+    return pg_boltz_plan_batched_ex(&o, ncell, N, M, S, kernel_gamma);
+}
+
+PG_API int pg_boltz_batched_offsets(const pg_boltz_plan_t *p, long long *offsets_host)
+{
+    if (!p || !p->batch || !offsets_host) return set_error(PG_ERR_ARG, "not a batched plan, or NULL output");
+    std::memcpy(offsets_host, p->batch->offsets.data(), sizeof(long long) * p->batch->offsets.size());
+    return PG_OK;
+}
+
+PG_API int pg_boltz_collide_batched(pg_boltz_plan_t *p, const double *f_dev, double *Q_dev)
+{
+    if (!p) return set_error(PG_ERR_ARG, "plan is NULL");
+    if (!p->batch) return set_error(PG_ERR_STATE, "pg_boltz_collide_batched needs a batched plan");
+    if (!f_dev || !Q_dev) return set_error(PG_ERR_ARG, "f or Q is NULL");
+    BatchState &B = *p->batch;
+    const long long modes = B.offsets.back();
+    const char *fb = reinterpret_cast<const char *>(f_dev);
+    const char *qb = reinterpret_cast<const char *>(Q_dev);
+    if (fb < qb + modes * 8 && qb < fb + modes * 8) return set_error(PG_ERR_ARG, "f and Q overlap");
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return set_error(PG_ERR_CUDA, "cannot select the plan's device");
+    int rc;
+    if (B.timing) cudaEventRecord(B.ev[0], p->stream);
+    if (!B.use_graph) {
+        if ((rc = enqueue_batch(p, p->stream, f_dev, Q_dev))) return rc;
+    } else {
+        if (!B.exec || B.g_f != f_dev || B.g_Q != Q_dev) {
+            // capture the launch sequence once per (f, Q) pair, then replay it
+            if (B.exec) {
+                cudaGraphExecDestroy(B.exec);
+                B.exec = nullptr;
+            }
+            if (B.graph) {
+                cudaGraphDestroy(B.graph);
+                B.graph = nullptr;
+            }
+            if (!B.cap_stream && (rc = cuda_check(cudaStreamCreateWithFlags(&B.cap_stream, cudaStreamNonBlocking),
+                                                  "capture stream")))
+                return rc;
+            if ((rc = cuda_check(cudaStreamBeginCapture(B.cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture")))
+                return rc;
+            rc = enqueue_batch(p, B.cap_stream, f_dev, Q_dev);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(B.cap_stream, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if ((rc = cuda_check(e, "end capture"))) return rc;
+            B.graph = g;
+            if ((rc = cuda_check(cudaGraphInstantiate(&B.exec, B.graph, 0), "graph instantiate"))) return rc;
+            B.g_f = f_dev;
+            B.g_Q = Q_dev;
+        }
+        if ((rc = cuda_check(cudaGraphLaunch(B.exec, p->stream), "graph launch"))) return rc;
+    }
+    if (B.timing) {
+        cudaEventRecord(B.ev[1], p->stream);
+        B.timed = true;
+    }
+    p->have_q = false;
+    return PG_OK;
+}
+
+PG_API int pg_boltz_batched_use_graph(pg_boltz_plan_t *p, int enable)
+{
+    if (!p || !p->batch) return set_error(PG_ERR_ARG, "not a batched plan");
+    p->batch->use_graph = enable != 0;
+    return PG_OK;
+}
+
+// Timing of batched plans (called by pg_boltz_set_timing / pg_boltz_stage_times): events around
+// the whole call (prep, spreading and finalisation), reported as the spreading stage.
+int pg_batched_timing(pg_boltz_plan_t *p, int enable)
+{
+    BatchState &B = *p->batch;
+    if (enable && !B.ev[0]) {
+        int rc;
+        if ((rc = cuda_check(cudaEventCreate(&B.ev[0]), "cudaEventCreate")) ||
+            (rc = cuda_check(cudaEventCreate(&B.ev[1]), "cudaEventCreate")))
+            return rc;
+    }
+    B.timing = enable != 0;
+    B.timed = false;
+    return PG_OK;
+}
+
+int pg_batched_elapsed(pg_boltz_plan_t *p, double *ms_out)
+{
+    BatchState &B = *p->batch;
+    if (!B.timed) return set_error(PG_ERR_STATE, "no timed batched collide since timing was enabled");
+    int rc = cuda_check(cudaEventSynchronize(B.ev[1]), "cudaEventSynchronize");
+    if (rc) return rc;
+    float ms = 0.0f;
+    if ((rc = cuda_check(cudaEventElapsedTime(&ms, B.ev[0], B.ev[1]), "cudaEventElapsedTime"))) return rc;
+    ms_out[0] = 0.0;
+    ms_out[1] = 0.0;
+    ms_out[2] = ms;
+    ms_out[3] = 0.0;
+    return PG_OK;
+}

@@ -29,7 +29,7 @@ struct SpreadArgs {
     const void *wsig;     // M sphere weights
     double Wsig;          // sum_m w_m
     const double *bound;  // device scalar B >= sum_p |q_p| (written by the loss kernel)
-    double prune_rel;     // pairs whose strength bound is below prune_rel * B / npairs are skipped (0: none)
+    const double *tau;    // device scalar: node pairs whose strength bound is below it are skipped (0: none)
     unsigned long long *grid;  // nf^d folded grid, int64 fixed point in units of 2^-Eg
     int simple_fold;      // 1 when w <= n/2: unfolded indices lie in [-n/2, n] (no modulo needed)
 };
@@ -42,6 +42,11 @@ __host__ __device__ inline int global_exponent(double B)
     return 60 - ilogb(B);
 }
 
+// Screening of negligible node pairs: the loss kernel counts the pair bounds per binary
+// exponent (kScreenBins bins, bin k holds bounds in [2^(k - kScreenOffset), 2^(k+1 - kScreenOffset)),
+// the first and last bins also everything below / above).
+constexpr int kScreenBins = 256;
+constexpr int kScreenOffset = 200;
 // Launch the spreading kernel for (precision, d, w); returns cudaSuccess or the launch error.
 // One translation unit per (precision, d) keeps the parallel build short.
 cudaError_t launch_spread_f32_d2(const SpreadArgs &a, int w, int blocks, int threads, size_t smem, cudaStream_t s);
@@ -70,12 +75,25 @@ cudaError_t launch_recon_last(const double *in, Dims3 in_dims, const double *A, 
                               const double *scale, int d, double *a, float *af, cudaStream_t s);
 // Loss: h_i = a_i * Lsum_i * prod_l inv_mu2[i_l], Lsum_i = Bw * sum_j a_j B(|v_i - v_j|);
 // also ub_i = |a_i| Bw sum_j |a_j| B_ij prod_l mu^-2(|c_l| + rad), an upper bound of the
-// spreading strengths of the pairs (i, .).
-cudaError_t launch_loss(const double *a, const double *vnode, int N, int d, double gamma,
+// spreading strengths of the pairs (i, .).  FP32 pair terms carry a relative error near 1e-7,
+// well inside the FP32 path's tolerance; the bound gets a 1e-5 margin in k_bound_reduce.
+// vnode32 != nullptr selects FP32 pair terms (the FP32 path).
+// hist != nullptr: also count every pair bound |a_i| Bw |a_j| B_ij prod mu^-2 into the screening histogram.
+cudaError_t launch_loss(const double *a, const double *vnode, const float *vnode32, int N, int d, double gamma,
                         int fast_gamma, double Bw, const double *inv_mu2, double S, int r,
-                        double *h, double *ub, cudaStream_t s);
-// B = sum_i ub_i (fixed summation order), written to *B.
-cudaError_t launch_bound_reduce(const double *ub, int n, double *B, cudaStream_t s);
+                        double *h, double *ub, unsigned long long *hist, cudaStream_t s);
+// Screening bin of a pair bound u > 0.
+__host__ __device__ inline int screen_bin(double u)
+{
+    int e = ilogb(u) + kScreenOffset;
+    return e < 0 ? 0 : (e >= kScreenBins ? kScreenBins - 1 : e);
+}
+// B = sum_i ub_i (fixed summation order), written to *B.  When hist != nullptr also the screening
+// threshold *tau = 2^(k - kScreenOffset) for the largest k with
+//   sum_{bins j < k} count_j 2^(j+1 - kScreenOffset) <= eps * B
+// (an upper bound of the total strength of the pairs below tau), else *tau = 0.
+cudaError_t launch_bound_reduce(const double *ub, int n, const unsigned long long *hist, double eps, double *B,
+                                double *tau, cudaStream_t s);
 // First transform pass reading the int64 fixed-point grid (units 2^-Eg, Eg from *B).
 cudaError_t launch_axis_pass_fixed(const unsigned long long *in, Dims3 in_dims, int ax, const double *A,
                                    int m, const double *B, double *out, cudaStream_t s);

@@ -14,266 +14,18 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <atomic>
 #include <cmath>
-#include <cstdarg>
-#include <cstdio>
 #include <cstring>
 #include <new>
-#include <string>
 #include <vector>
 
-#include "pg_boltz.h"
-#include "pgb_internal.cuh"
+#include "host.cuh"
 
 #define PG_API extern "C" __attribute__((visibility("default")))
 
-namespace {
-
-thread_local std::string g_last_error;
-std::atomic<int> g_fail_alloc_countdown{0};
-
-int set_error(int code, const char *fmt, ...)
-{
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof(buf), fmt, ap);
-    va_end(ap);
-    g_last_error = buf;
-    return code;
-}
-
-const double kPi = 3.14159265358979323846;
-
-// Make `dev` current for the lifetime of the guard and restore the caller's device.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) {
-            ok = false;
-            return;
-        }
-        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
-    }
-    ~DeviceGuard()
-    {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
-// Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on P_n).
-void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
-{
-    x.assign(n, 0.0);
-    w.assign(n, 0.0);
-    for (int i = 0; i < (n + 1) / 2; ++i) {
-        double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
-        double dp = 0.0;
-        for (int it = 0; it < 100; ++it) {
-            double p0 = 1.0, p1 = z;
-            for (int k = 2; k <= n; ++k) {
-                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
-                p0 = p1;
-                p1 = p2;
-            }
-            dp = n * (z * p1 - p0) / (z * z - 1.0);
-            double dz = p1 / dp;
-            z -= dz;
-            if (std::fabs(dz) < 1e-16) break;
-        }
-        double p0 = 1.0, p1 = z;
-        for (int k = 2; k <= n; ++k) {
-            double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
-            p0 = p1;
-            p1 = p2;
-        }
-        dp = n * (z * p1 - p0) / (z * z - 1.0);
-        x[i] = -z;
-        x[n - 1 - i] = z;
-        w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
-    }
-}
-
-}  // namespace
-
-int pgb::record_error(int code, const char *msg) { return set_error(code, "%s", msg); }
-
-struct pg_boltz_plan_s {
-    pg_boltz_info_t info{};
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    int d = 2, N = 2, M = 2, r = 1, prec = PG_PREC_FP64, Mp = 0;
-    double S = 1.0, gamma = 0.0, tol = 1e-6, sigma_up = 2.0;
-    int n = 0, nf = 0, w = 0;
-    double beta = 0.0;
-    int nnode = 0;
-    long long npairs = 0;
-    int fast_gamma = 0;
-    double Bconst = 0.0, Wsig = 0.0;
-    int nslab = 1, rows_per_slab = 0, spread_blocks = 0, spread_threads = 256;
-    size_t spread_smem = 0;
-    size_t device_bytes = 0;
-    std::vector<void *> allocs;
-    std::vector<double> proj_v;  // host copy of projection node velocities
-    bool have_q = false;
-    int last_launches = 0;
-    pgb::SpreadArgs sargs{};   // spreading-kernel arguments (fixed at plan time)
-    // optional per-stage timing: events recorded on the plan's stream around the stages
-    bool timing = false;
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    bool ev_recorded = false;
-
-    // device tables
-    double *R = nullptr;       // N x (N+1): T_k(xi_i)/sqrt(c_k), interior nodes
-    double *E = nullptr;       // (N+1) x N: transpose of R
-    double *Dm = nullptr;      // (N+1) x nf: cosine transform + deconvolution
-    double *Pm = nullptr;      // (N+1) x Mp: projection
-    double *scale_a = nullptr; // N: (pi/(N+1)) mu_i^2
-    double *inv_mu2 = nullptr; // N: 1/mu_i^2
-    double *v64 = nullptr;     // N node velocities
-    float *v32 = nullptr;
-    double *sig64 = nullptr, *wsig64 = nullptr;  // M x d, M
-    float *sig32 = nullptr, *wsig32 = nullptr;
-    // workspace
-    double *tA = nullptr, *tB = nullptr, *tC = nullptr, *tD = nullptr;
-    double *a64 = nullptr;
-    float *a32 = nullptr;
-    double *h = nullptr, *Qplus = nullptr, *Qlast = nullptr, *mom = nullptr;
-    double *ub = nullptr;      // N^d per-node strength bounds
-    double *bound = nullptr;   // scalar B >= sum_p |q_p| (follows the grid in one allocation)
-    unsigned long long *grid = nullptr;  // folded grid, int64 fixed point
-    double prune_rel = 0.0;
-};
+using namespace pgbh;
 
 namespace {
-
-int dev_alloc(pg_boltz_plan_t *p, void **ptr, size_t bytes)
-{
-    *ptr = nullptr;
-    int c = g_fail_alloc_countdown.load();
-    if (c > 0) {
-        if (g_fail_alloc_countdown.fetch_sub(1) == 1)
-            return set_error(PG_ERR_NOMEM, "device allocation of %zu bytes failed (injected)", bytes);
-    }
-    cudaError_t e = cudaMalloc(ptr, bytes < 16 ? 16 : bytes);
-    if (e != cudaSuccess) {
-        *ptr = nullptr;
-        cudaGetLastError();
-        return set_error(e == cudaErrorMemoryAllocation ? PG_ERR_NOMEM : PG_ERR_CUDA,
-                         "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
-    }
-    p->allocs.push_back(*ptr);
-    p->device_bytes += bytes;
-    return PG_OK;
-}
-
-template <typename T>
-int upload(pg_boltz_plan_t *p, T **dst, const std::vector<T> &src)
-{
-    int rc = dev_alloc(p, reinterpret_cast<void **>(dst), src.size() * sizeof(T));
-    if (rc) return rc;
-    cudaError_t e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return set_error(PG_ERR_CUDA, "upload failed: %s", cudaGetErrorString(e));
-    return PG_OK;
-}
-
-void free_plan(pg_boltz_plan_t *p)
-{
-    if (!p) return;
-    for (cudaEvent_t &e : p->ev)
-        if (e) cudaEventDestroy(e);
-    for (void *q : p->allocs) cudaFree(q);
-    p->allocs.clear();
-    delete p;
-}
-
-double ipow(double x, int k)
-{
-    double r = 1.0;
-    for (int i = 0; i < k; ++i) r *= x;
-    return r;
-}
-
-// Kernel width for precision tol at oversampling sigma.  The exponential-of-semicircle
-// spreading error decays like exp(-pi w sqrt(1 - 1/sigma)); the constants are fitted to
-// measured errors of the folded cosine transform against direct sums (0.9 decades per
-// unit of w at sigma = 2, 0.8 decades offset).
-int width_for(double tol, double sigma)
-{
-    double per_w = 0.9 * std::sqrt(2.0 * (1.0 - 1.0 / sigma));
-    int w = (int)std::ceil((-std::log10(tol) - 0.8) / per_w);
-    return std::max(w, pgb::kMinWidth);
-}
-
-// psi_hat(k) = int psi(x) cos(k x) dx with psi(x) = exp(beta (sqrt(1 - (x/alpha)^2) - 1)),
-// |x| < alpha = w pi / n.  With x = alpha sin(theta) the integrand is smooth:
-// alpha int_{-pi/2}^{pi/2} exp(beta (cos theta - 1)) cos(k alpha sin theta) cos theta dtheta.
-std::vector<double> kernel_ft(int N, int w, double beta, int n)
-{
-    std::vector<double> gx, gw;
-    gauss_legendre(256, gx, gw);
-    const double alpha = w * kPi / n;
-    std::vector<double> out(N + 1);
-    for (int k = 0; k <= N; ++k) {
-        double acc = 0.0;
-        for (size_t t = 0; t < gx.size(); ++t) {
-            double th = 0.5 * kPi * gx[t];
-            acc += gw[t] * std::exp(beta * (std::cos(th) - 1.0)) * std::cos(k * alpha * std::sin(th)) *
-                   std::cos(th);
-        }
-        out[k] = alpha * 0.5 * kPi * acc;
-    }
-    return out;
-}
-
-void sphere_points(int d, int M, int kind, std::vector<double> &pts, std::vector<double> &wts)
-{
-    pts.assign((size_t)M * d, 0.0);
-    if (d == 2) {
-        for (int m = 0; m < M; ++m) {
-            double th = 2.0 * kPi * m / M;
-            pts[2 * m] = std::cos(th);
-            pts[2 * m + 1] = std::sin(th);
-        }
-        wts.assign(M, 2.0 * kPi / M);
-        return;
-    }
-    const double golden = kPi * (3.0 - std::sqrt(5.0));
-    if (kind == PG_SPHERE_FIBONACCI) {
-        for (int m = 0; m < M; ++m) {
-            double z = 1.0 - (2.0 * m + 1.0) / M;
-            double rho = std::sqrt(1.0 - z * z);
-            pts[3 * m] = rho * std::cos(m * golden);
-            pts[3 * m + 1] = rho * std::sin(m * golden);
-            pts[3 * m + 2] = z;
-        }
-    } else {
-        const int h = M / 2;
-        for (int m = 0; m < h; ++m) {
-            double z = 1.0 - (2.0 * m + 1.0) / h;
-            double rho = std::sqrt(1.0 - z * z);
-            double x = rho * std::cos(m * golden), y = rho * std::sin(m * golden);
-            pts[3 * m] = x;
-            pts[3 * m + 1] = y;
-            pts[3 * m + 2] = z;
-            pts[3 * (m + h)] = -x;
-            pts[3 * (m + h) + 1] = -y;
-            pts[3 * (m + h) + 2] = -z;
-        }
-    }
-    wts.assign(M, 4.0 * kPi / M);
-}
-
-double map_v(double phi, double S, int r)
-{
-    // xi = -cos(phi); r = 1: v = S xi / sqrt(1 - xi^2) = -S cot(phi); r = 0: v = S atanh(xi) = S ln tan(phi/2)
-    if (r == 1) return -S * std::cos(phi) / std::sin(phi);
-    return S * std::log(std::tan(0.5 * phi));
-}
 
 int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
 {
@@ -285,8 +37,7 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
 
     // ---- transform / spreading parameters
     p->sigma_up = (o.upsampfac > 0.0) ? o.upsampfac : 2.0;
-    p->n = (int)std::ceil(p->sigma_up * (2 * N + 1));
-    if (p->n % 2) p->n += 1;
+    p->n = grid_size(N, p->sigma_up);
     p->nf = p->n / 2 + 1;
     p->w = width_for(p->tol, p->sigma_up);
     const int wmax = (p->prec == PG_PREC_FP32) ? pgb::kMaxWidthF32 : pgb::kMaxWidthF64;
@@ -294,36 +45,13 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
         if (p->prec == PG_PREC_FP32) p->w = wmax;  // FP32 spreading cannot resolve more anyway
         else return set_error(PG_ERR_ARG, "tol %g needs kernel width %d > %d", p->tol, p->w, wmax);
     }
-    p->beta = 0.97 * kPi * (1.0 - 0.5 / p->sigma_up) * p->w;
+    p->beta = kernel_beta(p->w, p->sigma_up);
     p->Mp = (o.proj_nodes > 0) ? o.proj_nodes : 4 * (N + 1);
 
-    // ---- node tables
-    std::vector<double> R((size_t)N * (N + 1)), E((size_t)(N + 1) * N), sa(N), im(N), v(N);
-    std::vector<float> vf(N);
-    const double wnode = kPi / (N + 1);
-    for (int i = 0; i < N; ++i) {
-        const double phi = kPi * (i + 1) / (N + 1);
-        const double mu2 = ipow(std::sin(phi), 1 + p->r) / p->S;
-        sa[i] = wnode * mu2;
-        im[i] = 1.0 / mu2;
-        v[i] = map_v(phi, p->S, p->r);
-        vf[i] = (float)v[i];
-        for (int k = 0; k <= N; ++k) {
-            const double tk = std::cos(k * (kPi - phi)) / std::sqrt(k == 0 ? kPi : 0.5 * kPi);
-            R[(size_t)i * (N + 1) + k] = tk;
-            E[(size_t)k * N + i] = tk;
-        }
-    }
-    // ---- cosine transform with deconvolution: D[k][g] = (2 pi/n) cos(2 pi k g/n) / (sqrt(c_k) psi_hat(k))
-    std::vector<double> ph = kernel_ft(N, p->w, p->beta, p->n);
-    std::vector<double> D((size_t)(N + 1) * p->nf);
-    for (int k = 0; k <= N; ++k) {
-        const double ck = std::sqrt(k == 0 ? kPi : 0.5 * kPi);
-        for (int g = 0; g < p->nf; ++g) {
-            const long long kg = ((long long)k * g) % p->n;
-            D[(size_t)k * p->nf + g] = (2.0 * kPi / p->n) * std::cos(2.0 * kPi * (double)kg / p->n) / (ck * ph[k]);
-        }
-    }
+    // ---- node tables and the cosine transform with deconvolution
+    NodeTables nt = node_tables(N, p->S, p->r);
+    std::vector<float> vf(nt.v.begin(), nt.v.end());
+    std::vector<double> D = transform_matrix(N, p->n, p->w, p->beta);
     // ---- projection (Chebyshev-Gauss): P[k][p] = (pi/Mp) mu_p^-4 T_k(xi_p) / sqrt(c_k)
     const int Mp = p->Mp;
     std::vector<double> P((size_t)(N + 1) * Mp);
@@ -343,9 +71,10 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
     std::vector<float> spf(sp.begin(), sp.end()), swf(sw.begin(), sw.end());
 
     int rc;
-    if ((rc = upload(p, &p->R, R)) || (rc = upload(p, &p->E, E)) || (rc = upload(p, &p->Dm, D)) ||
-        (rc = upload(p, &p->Pm, P)) || (rc = upload(p, &p->scale_a, sa)) || (rc = upload(p, &p->inv_mu2, im)) ||
-        (rc = upload(p, &p->v64, v)) || (rc = upload(p, &p->v32, vf)) || (rc = upload(p, &p->sig64, sp)) ||
+    if ((rc = upload(p, &p->R, nt.R)) || (rc = upload(p, &p->E, nt.E)) || (rc = upload(p, &p->Dm, D)) ||
+        (rc = upload(p, &p->Pm, P)) || (rc = upload(p, &p->scale_a, nt.scale_a)) ||
+        (rc = upload(p, &p->inv_mu2, nt.inv_mu2)) || (rc = upload(p, &p->v64, nt.v)) ||
+        (rc = upload(p, &p->v32, vf)) || (rc = upload(p, &p->sig64, sp)) ||
         (rc = upload(p, &p->wsig64, sw)) || (rc = upload(p, &p->sig32, spf)) || (rc = upload(p, &p->wsig32, swf)))
         return rc;
 
@@ -360,12 +89,15 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
         (rc = dev_alloc(p, (void **)&p->a64, (size_t)p->nnode * 8)) ||
         (rc = dev_alloc(p, (void **)&p->a32, (size_t)p->nnode * 4)) ||
         (rc = dev_alloc(p, (void **)&p->h, (size_t)p->nnode * 8)) ||
-        (rc = dev_alloc(p, (void **)&p->grid, grid_cells * 8 + 8)) ||
+        (rc = dev_alloc(p, (void **)&p->grid, grid_cells * 8 + 16 + pgb::kScreenBins * 8)) ||
         (rc = dev_alloc(p, (void **)&p->ub, (size_t)p->nnode * 8)) ||
         (rc = dev_alloc(p, (void **)&p->Qplus, modes * 8)) || (rc = dev_alloc(p, (void **)&p->Qlast, modes * 8)) ||
         (rc = dev_alloc(p, (void **)&p->mom, 8 * 8)))
         return rc;
+    // one allocation: [grid | B | tau | screening histogram], cleared by one memset per call
     p->bound = reinterpret_cast<double *>(p->grid + grid_cells);
+    p->tau = p->bound + 1;
+    p->hist = reinterpret_cast<unsigned long long *>(p->tau + 1);
 
     // ---- spreading launch shape
     cudaDeviceProp prop;
@@ -426,7 +158,7 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
     ka.wsig = f32 ? (const void *)p->wsig32 : (const void *)p->wsig64;
     ka.Wsig = p->Wsig;
     ka.bound = p->bound;
-    ka.prune_rel = p->prune_rel;
+    ka.tau = p->tau;
     ka.grid = p->grid;
     ka.simple_fold = (p->w <= p->n / 2) ? 1 : 0;
     return PG_OK;
@@ -449,27 +181,6 @@ int validate(const pg_boltz_opts_t &o)
     if (o.proj_nodes < 0 || o.proj_nodes > 4096) return set_error(PG_ERR_ARG, "proj_nodes out of range");
     if (o.screen != 0 && o.screen != 1) return set_error(PG_ERR_ARG, "screen must be 0 or 1");
     return PG_OK;
-}
-
-pgb::Dims3 dims_of(int d, int a, int b, int c)
-{
-    pgb::Dims3 x;
-    if (d == 2) {
-        x.e[0] = 1;
-        x.e[1] = b;
-        x.e[2] = c;
-    } else {
-        x.e[0] = a;
-        x.e[1] = b;
-        x.e[2] = c;
-    }
-    return x;
-}
-
-int cuda_check(cudaError_t e, const char *what)
-{
-    if (e == cudaSuccess) return PG_OK;
-    return set_error(PG_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
 // Contract every axis but the last of `in` (shape `dims`, the last d axes live) with A,
@@ -496,13 +207,9 @@ int leading_passes(pg_boltz_plan_t *p, const double *in, pgb::Dims3 &dims, const
 
 // ============================================================================ ABI
 
-PG_API const char *pg_boltz_last_error(void) { return g_last_error.c_str(); }
-
-PG_API void pg_boltz_debug_fail_alloc(int countdown) { g_fail_alloc_countdown.store(countdown > 0 ? countdown : 0); }
-
 PG_API pg_boltz_plan_t *pg_boltz_plan_ex(const pg_boltz_opts_t *opts)
 {
-    g_last_error.clear();
+    set_error(PG_OK, "%s", "");
     if (!opts) {
         set_error(PG_ERR_ARG, "opts is NULL");
         return nullptr;
@@ -529,7 +236,7 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_ex(const pg_boltz_opts_t *opts)
     p->r = o.map_log ? 0 : 1;
     p->prec = (o.precision == PG_PREC_AUTO) ? (o.tol < 1e-8 ? PG_PREC_FP64 : PG_PREC_FP32) : o.precision;
     p->info.sphere = (o.d == 3) ? (o.sphere == PG_SPHERE_AUTO ? PG_SPHERE_ANTIPODAL : o.sphere) : PG_SPHERE_AUTO;
-    p->prune_rel = o.screen ? 1e-3 * o.tol : 0.0;
+    p->screen_eps = o.screen ? 0.05 * o.tol : 0.0;
     if (build_plan(p, o)) {
         free_plan(p);
         return nullptr;
@@ -583,6 +290,7 @@ PG_API int pg_boltz_set_stream(pg_boltz_plan_t *plan, void *cuda_stream)
 PG_API int pg_boltz_collide(pg_boltz_plan_t *p, const double *f_dev, double *Q_dev)
 {
     if (!p) return set_error(PG_ERR_ARG, "plan is NULL");
+    if (p->batch) return set_error(PG_ERR_STATE, "batched plans take pg_boltz_collide_batched");
     if (!f_dev || !Q_dev) return set_error(PG_ERR_ARG, "f or Q is NULL");
     const long long modes = (long long)ipow(p->N + 1, p->d);
     const char *fb = reinterpret_cast<const char *>(f_dev);
@@ -610,13 +318,20 @@ PG_API int pg_boltz_collide(pg_boltz_plan_t *p, const double *f_dev, double *Q_d
     // 2. clear the fixed-point grid and its bound; loss weights h_i = a_i L_i / mu_i^2 (Eq. Qminus,
     //    inner sum over v_*, sigma) and the strength bound B >= sum_p |q_p|
     const size_t grid_bytes = (size_t)ipow(p->nf, d) * 8;
-    if ((rc = cuda_check(cudaMemsetAsync(p->grid, 0, grid_bytes + 8, p->stream), "memset grid"))) return rc;
-    ++launches;
-    if ((rc = cuda_check(pgb::launch_loss(p->a64, p->v64, N, d, p->gamma, p->fast_gamma, p->Bconst * p->Wsig,
-                                          p->inv_mu2, p->S, p->r, p->h, p->ub, p->stream), "loss")))
+    if ((rc = cuda_check(cudaMemsetAsync(p->grid, 0, grid_bytes + 16 + pgb::kScreenBins * 8, p->stream),
+                         "memset grid")))
         return rc;
     ++launches;
-    if ((rc = cuda_check(pgb::launch_bound_reduce(p->ub, p->nnode, p->bound, p->stream), "bound"))) return rc;
+    if ((rc = cuda_check(pgb::launch_loss(p->a64, p->v64, f32 ? p->v32 : nullptr, N, d, p->gamma, p->fast_gamma,
+                                          p->Bconst * p->Wsig, p->inv_mu2, p->S, p->r, p->h, p->ub,
+                                          p->screen_eps > 0.0 ? p->hist : nullptr, p->stream),
+                         "loss")))
+        return rc;
+    ++launches;
+    if ((rc = cuda_check(pgb::launch_bound_reduce(p->ub, p->nnode, p->screen_eps > 0.0 ? p->hist : nullptr,
+                                                  p->screen_eps, p->bound, p->tau, p->stream),
+                         "bound")))
+        return rc;
     ++launches;
     mark(2);
     // 3. spread the M N^(2d) post-collision points onto the folded grid   (Eq. num_fast_k, Eq. nufft)
@@ -680,6 +395,7 @@ PG_API int pg_boltz_moments(pg_boltz_plan_t *p, double *out_host)
 PG_API int pg_boltz_set_timing(pg_boltz_plan_t *p, int enable)
 {
     if (!p) return set_error(PG_ERR_ARG, "plan is NULL");
+    if (p->batch) return pg_batched_timing(p, enable);
     DeviceGuard guard(p->device);
     if (!guard.ok) return set_error(PG_ERR_CUDA, "cannot select the plan's device");
     if (enable && !p->ev[0]) {
@@ -696,6 +412,7 @@ PG_API int pg_boltz_set_timing(pg_boltz_plan_t *p, int enable)
 PG_API int pg_boltz_stage_times(pg_boltz_plan_t *p, double *ms_out)
 {
     if (!p || !ms_out) return set_error(PG_ERR_ARG, "NULL argument");
+    if (p->batch) return pg_batched_elapsed(p, ms_out);
     if (!p->ev_recorded) return set_error(PG_ERR_STATE, "no timed pg_boltz_collide since timing was enabled");
     DeviceGuard guard(p->device);
     if (!guard.ok) return set_error(PG_ERR_CUDA, "cannot select the plan's device");
@@ -712,6 +429,7 @@ PG_API int pg_boltz_stage_times(pg_boltz_plan_t *p, double *ms_out)
 PG_API int pg_boltz_project_nodes(const pg_boltz_plan_t *p, double *v_host, int *count_out)
 {
     if (!p) return set_error(PG_ERR_ARG, "plan is NULL");
+    if (p->batch) return set_error(PG_ERR_STATE, "projection is not available on batched plans");
     if (count_out) *count_out = p->Mp;
     if (v_host) std::memcpy(v_host, p->proj_v.data(), sizeof(double) * p->Mp);
     return PG_OK;
@@ -720,6 +438,7 @@ PG_API int pg_boltz_project_nodes(const pg_boltz_plan_t *p, double *v_host, int 
 PG_API int pg_boltz_project(pg_boltz_plan_t *p, const double *fvals_dev, double *ftilde_dev)
 {
     if (!p) return set_error(PG_ERR_ARG, "plan is NULL");
+    if (p->batch) return set_error(PG_ERR_STATE, "projection is not available on batched plans");
     if (!fvals_dev || !ftilde_dev) return set_error(PG_ERR_ARG, "NULL device pointer");
     DeviceGuard guard(p->device);
     if (!guard.ok) return set_error(PG_ERR_CUDA, "cannot select the plan's device");

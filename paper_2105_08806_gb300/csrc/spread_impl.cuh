@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(kMaxThreadsF32) k_spread_f32(const __grid_cons
     const int Et = min(Eg - 10, 120);
     const int shift = Eg - Et;
     const float sc = (float)ldexp(1.0, Et);
-    const float tau = (float)(p.prune_rel * Bnd / (double)p.npairs);
+    const float tau = (float)*p.tau;
     long long first, nthr;
     pair_schedule(p, first, nthr);
     for (long long pr = first; pr < p.npairs; pr += nthr) {
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(kMaxThreadsF64) k_spread_f64(const __grid_cons
     __syncthreads();
     const double Bnd = *p.bound;
     const int Eg = global_exponent(Bnd);
-    const double tau = p.prune_rel * Bnd / (double)p.npairs;
+    const double tau = *p.tau;
     long long first, nthr;
     pair_schedule(p, first, nthr);
     for (long long pr = first; pr < p.npairs; pr += nthr) {

@@ -95,14 +95,21 @@ constexpr int kLossThreads = 128;
 //   ub_i   = |a_i| Bw sum_j |a_j| |v_i - v_j|^gamma prod_l mu^-2(|c_l| + rad)
 // where c = (v_i + v_j)/2, rad = |v_i - v_j|/2: every post-collision point of the pair lies
 // in the box |v'_l| <= |c_l| + rad and mu^-2 grows with |v|, so ub_i bounds the spreading
-// strengths sum_{j,m} |q_ijm| (times Bconst, which Bw carries).
+// strengths sum_{j,m} |q_ijm| (times Bconst, which Bw carries).  PT is the arithmetic of the
+// pair terms: FP64, or FP32 for the FP32 path, where 64-term partial sums are FP32 and
+// everything above them FP64.
+template <typename PT>
 __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict__ a,
-                                                        const double *__restrict__ vnode, int N,
-                                                        int d, double gamma, int fast_gamma,
-                                                        double Bw, const double *__restrict__ inv_mu2,
-                                                        double S, int r, double *__restrict__ h,
-                                                        double *__restrict__ ub)
+                                                        const PT *__restrict__ vnode, int N, int d,
+                                                        double gamma, int fast_gamma, double Bw,
+                                                        const double *__restrict__ inv_mu2, double S, int r,
+                                                        double *__restrict__ h, double *__restrict__ ub,
+                                                        unsigned long long *__restrict__ hist)
 {
+    __shared__ unsigned s_hist[kScreenBins];
+    if (hist)
+        for (int k = threadIdx.x; k < kScreenBins; k += blockDim.x) s_hist[k] = 0u;
+    __syncthreads();
     const int nnode = (d == 2) ? N * N : N * N * N;
     const int i = blockIdx.x;
     int idx[3] = {0, 0, 0};
@@ -113,36 +120,46 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict_
             t /= N;
         }
     }
-    double vi[3];
-    for (int l = 0; l < 3; ++l) vi[l] = (l < d) ? vnode[idx[l]] : 0.0;
-    const double invS = 1.0 / S;
+    PT vi[3];
+    for (int l = 0; l < 3; ++l) vi[l] = (l < d) ? vnode[idx[l]] : PT(0);
+    const PT Sp = PT(S), invS = PT(1) / Sp, gam = PT(gamma);
+    const double ai_w = fabs(a[i]) * Bw;  // pair bound = ai_w * |a_j| B_ij prod mu^-2
     double acc = 0.0, bnd = 0.0;
-    for (int j = threadIdx.x; j < nnode; j += blockDim.x) {
-        int t = j;
-        double g2 = 0.0, vj[3] = {0.0, 0.0, 0.0};
-        for (int l = d - 1; l >= 0; --l) {
-            vj[l] = vnode[t % N];
-            t /= N;
-            const double dl = vi[l] - vj[l];
-            g2 += dl * dl;
-        }
-        double B;
-        switch (fast_gamma) {
-        case 0: B = 1.0; break;
-        case 1: B = sqrt(g2); break;
-        case 2: B = sqrt(sqrt(g2)); break;
-        default: B = (g2 > 0.0) ? pow(g2, 0.5 * gamma) : 0.0; break;
-        }
-        acc = fma(a[j], B, acc);
-        if (a[j] != 0.0 && B != 0.0) {
-            const double rad = 0.5 * sqrt(g2);
-            double mu = 1.0;
-            for (int l = 0; l < d; ++l) {
-                const double R = fabs(0.5 * (vi[l] + vj[l])) + rad;
-                mu *= (r == 1) ? (S * S + R * R) * invS : S * cosh(R * invS);
+    for (int j0 = threadIdx.x * 64; j0 < nnode; j0 += blockDim.x * 64) {
+        PT lp = PT(0), bp = PT(0);
+        const int j1 = min(j0 + 64, nnode);
+        for (int j = j0; j < j1; ++j) {
+            int t = j;
+            PT g2 = PT(0), vj[3] = {PT(0), PT(0), PT(0)};
+            for (int l = d - 1; l >= 0; --l) {
+                vj[l] = vnode[t % N];
+                t /= N;
+                const PT dl = vi[l] - vj[l];
+                g2 += dl * dl;
             }
-            bnd = fma(fabs(a[j]) * B, mu, bnd);
+            const PT g = sqrt(g2);
+            PT B;
+            switch (fast_gamma) {
+            case 0: B = PT(1); break;
+            case 1: B = g; break;
+            case 2: B = sqrt(g); break;
+            default: B = (g2 > PT(0)) ? pow(g, gam) : PT(0); break;
+            }
+            const PT aj = PT(a[j]);
+            lp += aj * B;
+            if (aj != PT(0) && B != PT(0)) {
+                PT mu = PT(1);
+                for (int l = 0; l < d; ++l) {
+                    const PT R = fabs(PT(0.5) * (vi[l] + vj[l])) + PT(0.5) * g;
+                    mu *= (r == 1) ? (Sp * Sp + R * R) * invS : Sp * cosh(R * invS);
+                }
+                const PT u = fabs(aj) * B * mu;
+                bp += u;
+                if (hist) atomicAdd(&s_hist[screen_bin(ai_w * (double)u)], 1u);
+            }
         }
+        acc += (double)lp;
+        bnd += (double)bp;
     }
     const double tot = block_sum<kLossThreads>(acc);
     const double tb = block_sum<kLossThreads>(bnd);
@@ -152,19 +169,41 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict_
         h[i] = a[i] * Bw * tot * sc;
         ub[i] = fabs(a[i]) * Bw * tb;
     }
+    if (hist) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < kScreenBins; k += blockDim.x)
+            if (s_hist[k]) atomicAdd(hist + k, (unsigned long long)s_hist[k]);
+    }
 }
 
 constexpr int kReduceThreads = 1024;
 
-// B = (1 + 1e-6) sum_i ub_i in a fixed order (deterministic); the factor covers FP32 rounding
-// of the strengths in the FP32 spreading kernel.
+// B = (1 + 1e-5) sum_i ub_i in a fixed order (deterministic); the factor covers FP32 rounding
+// of the pair terms and of the strengths in the FP32 spreading kernel.
 __global__ void __launch_bounds__(kReduceThreads) k_bound_reduce(const double *__restrict__ ub, int n,
-                                                                  double *__restrict__ B)
+                                                                  const unsigned long long *__restrict__ hist,
+                                                                  double eps, double *__restrict__ B,
+                                                                  double *__restrict__ tau)
 {
     double s = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) s += ub[i];
     const double tot = block_sum<kReduceThreads>(s);
-    if (threadIdx.x == 0) *B = tot * (1.0 + 1e-6);
+    if (threadIdx.x == 0) {
+        const double Bv = tot * (1.0 + 1e-5);
+        *B = Bv;
+        double t = 0.0;
+        if (hist && Bv > 0.0) {
+            double cum = 0.0;
+            int k = 0;
+            for (; k < kScreenBins - 1; ++k) {
+                const double add = (double)hist[k] * ldexp(1.0, k + 1 - kScreenOffset);
+                if (cum + add > eps * Bv) break;
+                cum += add;
+            }
+            t = ldexp(1.0, k - kScreenOffset);
+        }
+        *tau = t;
+    }
 }
 
 // First transform pass over the int64 fixed-point grid: out = (A . in) 2^-Eg.
@@ -296,18 +335,24 @@ cudaError_t launch_recon_last(const double *in, Dims3 in_dims, const double *A, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_loss(const double *a, const double *vnode, int N, int d, double gamma,
+cudaError_t launch_loss(const double *a, const double *vnode, const float *vnode32, int N, int d, double gamma,
                         int fast_gamma, double Bw, const double *inv_mu2, double S, int r, double *h,
-                        double *ub, cudaStream_t s)
+                        double *ub, unsigned long long *hist, cudaStream_t s)
 {
     const int nnode = (d == 2) ? N * N : N * N * N;
-    k_loss<<<nnode, kLossThreads, 0, s>>>(a, vnode, N, d, gamma, fast_gamma, Bw, inv_mu2, S, r, h, ub);
+    if (vnode32)
+        k_loss<float><<<nnode, kLossThreads, 0, s>>>(a, vnode32, N, d, gamma, fast_gamma, Bw, inv_mu2, S, r, h, ub,
+                                                     hist);
+    else
+        k_loss<double><<<nnode, kLossThreads, 0, s>>>(a, vnode, N, d, gamma, fast_gamma, Bw, inv_mu2, S, r, h, ub,
+                                                      hist);
     return cudaGetLastError();
 }
 
-cudaError_t launch_bound_reduce(const double *ub, int n, double *B, cudaStream_t s)
+cudaError_t launch_bound_reduce(const double *ub, int n, const unsigned long long *hist, double eps, double *B,
+                                double *tau, cudaStream_t s)
 {
-    k_bound_reduce<<<1, kReduceThreads, 0, s>>>(ub, n, B);
+    k_bound_reduce<<<1, kReduceThreads, 0, s>>>(ub, n, hist, eps, B, tau);
     return cudaGetLastError();
 }
 

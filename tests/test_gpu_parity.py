@@ -98,13 +98,14 @@ def test_slabbed_3d_grid_fp64():
 
 def test_full_size_2d_hard_spheres_fp32_sampled_modes():
     """The 2D hard-sphere workload at full size (N = 64, M = 32, S = 3) in the FP32 spreading
-    path, compared on a seeded mode subset the oracle computes one by one."""
+    path with the plan bench.py times (tol 1e-6), compared on a seeded mode subset the oracle
+    computes one by one."""
     w = W.c2_2d_vhs()
     d, N, M, S, gamma = w.d, w.N, w.M, w.S, w.gamma
     ft = O.project(w, d, N, S, 1).ravel()
     modes = sample_modes(d, N, 48, seed=11)
     gain, loss = O.collide_parts(ft, d, N, M, S, gamma, r=1, modes=modes)
-    Q, info, mom = gpu_collide(ft, d, N, M, S, gamma, 1e-7, precision=PG_PREC_FP32)
+    Q, info, mom = gpu_collide(ft, d, N, M, S, gamma, 1e-6, precision=PG_PREC_FP32)  # bench.py's plan
     assert info["points"] == M * N ** (2 * d)
     assert rel_l2(Q[flat_index(modes, N)], gain - loss) < TOL32
     ma, en = O.mass_energy_coeffs(d, N, S)
@@ -183,3 +184,26 @@ def test_alloc_failure_injection_leaves_no_plan():
     lib().pg_boltz_debug_fail_alloc(0)
     with Plan(2, 8, 8, 2.0, 0.0, 1e-6):
         pass
+
+
+@pytest.mark.parametrize("prec", [PG_PREC_FP64, PG_PREC_FP32])
+def test_screened_pairs_stay_within_tolerance(prec):
+    """screen=1 skips the node pairs with the smallest strength bounds (their summed bound at
+    most 0.05 tol B); results must stay within the same bars against the oracle."""
+    d, N, M, S, gamma = 2, 24, 16, 3.0, 1.0
+    ft = O.project(W.c2_2d_vhs(), d, N, S, 1).ravel()
+    gain, loss = O.collide_parts(ft, d, N, M, S, gamma, r=1)
+    tol = 1e-13 if prec == PG_PREC_FP64 else 1e-6
+    Q, info, _ = gpu_collide(ft, d, N, M, S, gamma, tol, precision=prec, screen=True)
+    err = rel_l2(Q, gain - loss)
+    assert err < (TOL64 if prec == PG_PREC_FP64 else TOL32), err
+
+
+def test_full_size_2d_hard_spheres_fp32_screened_sampled_modes():
+    w = W.c2_2d_vhs()
+    d, N, M, S, gamma = w.d, w.N, w.M, w.S, w.gamma
+    ft = O.project(w, d, N, S, 1).ravel()
+    modes = sample_modes(d, N, 48, seed=11)
+    gain, loss = O.collide_parts(ft, d, N, M, S, gamma, r=1, modes=modes)
+    Q, info, mom = gpu_collide(ft, d, N, M, S, gamma, 1e-6, precision=PG_PREC_FP32, screen=True)
+    assert rel_l2(Q[flat_index(modes, N)], gain - loss) < TOL32
