@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--tol32", type=float, default=1e-6)
     ap.add_argument("--upsampfac", type=float, default=0.0)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=2)
     return ap.parse_args()
 
 
@@ -137,6 +139,59 @@ def cpu_baseline(workload, budget_s=12.0):
                       f"in {dt2:.2f} s, scaled by {nnode}/{n2}"}
 
 
+# ------------------------------------------------------------------ batched
+def run_batched(steps, stream, dev):
+    """The 4096-cell batched 2D workload: N in {16,24,32}, M in {8,16,32}, gamma in {0,1}, S=3,
+    FP32 spreading (tol 1e-6), one graph-replayed pg_boltz_collide_batched per step."""
+    import numpy as np
+    import torch
+
+    from paper_2105_08806_gb300 import PG_PREC_FP32, BatchedPlan, Plan
+    from paper_2105_08806_gb300 import workloads as Wl
+
+    cells = Wl.c5_batched_2d()
+    d = 2
+    fts, plans = [], {}
+    for w in cells:  # each cell's density projected on the GPU with a plan of its N
+        if w.N not in plans:
+            plans[w.N] = Plan(d, w.N, 8, w.S, 0.0, 1e-6)
+            plans[w.N].set_stream(stream)
+        pl = plans[w.N]
+        v = np.array(pl.project_nodes())
+        G = np.meshgrid(v, v, indexing="ij")
+        fv = torch.as_tensor(w(np.stack([x.ravel() for x in G], 1)), device=dev)
+        out = torch.empty((w.N + 1) ** d, dtype=torch.float64, device=dev)
+        with torch.cuda.stream(stream):
+            pl.project(fv, out)
+        fts.append(out)
+    stream.synchronize()
+    for pl in plans.values():
+        pl.close()
+    f = torch.cat(fts)
+    Q = torch.empty_like(f)
+    bp = BatchedPlan(d, [w.N for w in cells], [w.M for w in cells], [w.S for w in cells],
+                     [w.gamma for w in cells], 1e-6, precision=PG_PREC_FP32)
+    bp.set_stream(stream)
+    info = bp.info()
+    bp.collide(f, Q)  # capture + first replay
+    stream.synchronize()
+    ms = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        bp.collide(f, Q)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    bp.close()
+    t = statistics.mean(ms)
+    return {"cells": len(cells), "ms_per_batch": t, "cell_evals_per_s": len(cells) * 1000.0 / t,
+            "points_per_s": info["points"] * 1000.0 / t, "points_per_batch": info["points"],
+            "spread_blocks": info["spread_blocks"], "spread_threads": info["spread_threads"],
+            "steps": steps, "launches_per_call": info["launches_per_collide"],
+            "workload": "4096 2D cells, N in {16,24,32}, M in {8,16,32}, gamma in {0,1}, S=3, FP32 tol 1e-6, CUDA graph"}
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
@@ -206,6 +261,11 @@ def run_ours(args):
         ms32, st32, wall32 = timed_loop(plan32, Q, args.steps, args.warmup)
     clocks = clk.summary()
     ms64, st64, _ = timed_loop(plan64, Q64, max(1, args.fp64_steps), 1)
+    # screened variant of the FP32 path (skips the node pairs with the smallest strength bounds)
+    plan_sc = Plan(d, N, M, S, gamma, args.tol32, precision=PG_PREC_FP32, upsampfac=args.upsampfac, screen=True)
+    plan_sc.set_stream(stream)
+    Qsc = torch.empty_like(ft)
+    ms_sc, _, _ = timed_loop(plan_sc, Qsc, args.steps, args.warmup)
 
     # end to end through the public API: pinned host f~ in, host Q out, every step
     fh = ft.cpu().pin_memory()
@@ -235,6 +295,9 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         mean32, mean_e2e = float(t[0]), float(t[1])
     err = float(torch.linalg.norm(Q - Q64) / torch.linalg.norm(Q64))
+    err_sc = float(torch.linalg.norm(Qsc - Q64) / torch.linalg.norm(Q64))
+    plan_sc.close()
+    batched = None if args.no_batched else run_batched(max(1, args.batched_steps), stream, dev)
     mom = plan64.moments()
 
     # roofline of the dominant kernel (spreading): one shared-memory atomic add per
@@ -281,6 +344,10 @@ def run_ours(args):
         "fp64_path": {"value": 1000.0 / statistics.mean(ms64), "ms_per_step": statistics.mean(ms64),
                       "steps": len(ms64), "kernel_width": info64["kernel_width"], "stages_ms": stage_mean64},
         "speedup_fp32_vs_fp64": statistics.mean(ms64) / mean32,
+        "screened": {"value": 1000.0 / statistics.mean(ms_sc), "ms_per_step": statistics.mean(ms_sc),
+                     "rel_err_vs_fp64_path": err_sc,
+                     "note": "screen=1: node pairs whose summed strength bound is below 0.05 tol B are skipped"},
+        "batched": batched,
         "stages_ms": stage_mean32,
         "conservation_fp64": {"mass_rel": abs(mom["mass"]) / abs(mom["mass_gain"]),
                               "energy_rel": abs(mom["energy"]) / abs(mom["energy_gain"])},
