@@ -86,18 +86,25 @@ __device__ __forceinline__ int fold_index(int u, int n)
 // Unfolded index u -> folded cell; `simple` when u is known to lie in [-n/2, n].
 __device__ __forceinline__ int fold_cell(int u, int n, bool simple)
 {
-    if (simple) {
-        u = (u < 0) ? -u : u;
-        return (u > (n >> 1)) ? n - u : u;
+    if (simple) {  // u in [-n/2, n]: fold(u) = min(|u|, n - |u|)
+        u = abs(u);
+        return min(u, n - u);
     }
     return fold_index(u, n);
 }
 
 // The w kernel weights psi(x_u - z) of one axis, u = s..s+w-1, in units where one grid cell
 // is 1 and x = z n / (2 pi): psi = exp(beta (sqrt(1 - t^2) - 1)), t = (u - x) 2/w.
+template <int W>
+__device__ __forceinline__ void axis_weights_f32(const SpreadArgs &p, float x, float *wt, int *idx);
+
 template <typename T, int W>
 __device__ __forceinline__ void axis_weights(const SpreadArgs &p, T x, T *wt, int *idx)
 {
+    if constexpr (sizeof(T) == 4) {
+        axis_weights_f32<W>(p, x, wt, idx);
+        return;
+    }
     const int s = (int)Fn<T>::floor_(x - T(0.5 * W)) + 1;
     const T inv_hw = T(2.0 / W);
     const T beta = T(p.beta);
@@ -107,6 +114,84 @@ __device__ __forceinline__ void axis_weights(const SpreadArgs &p, T x, T *wt, in
         const T t = (T(s + a) - x) * inv_hw;
         const T one_m = T(1) - t * t;
         wt[a] = one_m > T(0) ? Fn<T>::exp_(beta * (Fn<T>::sqrt_pos(one_m) - T(1))) : T(0);
+        idx[a] = fold_cell(s + a, p.n, simple);
+    }
+}
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// atan(t) for t >= 0: t P(t^2) on [0, 1] and pi/2 - atan(1/t) above.  P is a degree-8
+// polynomial in t^2 fitted to atan(t)/t on [0, 1] by iteratively reweighted least squares
+// (towards the minimax error of t P(t^2)); its error is below 1e-7 when evaluated in FP32.
+__device__ __forceinline__ float atan_pos_f32(float t)
+{
+    const bool inv = t > 1.0f;
+    const float u = inv ? rcp_approx(t) : t;
+    const float x = u * u;
+    float p = 0.002455897797786189f;
+    p = fmaf(p, x, -0.014397678937342222f);
+    p = fmaf(p, x, 0.03977441675320232f);
+    p = fmaf(p, x, -0.07234180246738538f);
+    p = fmaf(p, x, 0.10498555283788273f);
+    p = fmaf(p, x, -0.1416109770841035f);
+    p = fmaf(p, x, 0.19985882274088168f);
+    p = fmaf(p, x, -0.33332594819936656f);
+    p = fmaf(p, x, 0.9999998857035092f);
+    const float r = u * p;
+    return inv ? 1.5707963267948966f - r : r;
+}
+
+// FP32 angle z = arccos(xi(v)) and weight mu(xi(v))^-2 of one mapped coordinate (Section 2.1):
+//   r = 1: z = pi/2 - atan(v/S),          mu^-2 = (S^2 + v^2)/S
+//   r = 0: z = 2 atan(exp(-v/S)),         mu^-2 = S (exp(v/S) + exp(-v/S))/2
+__device__ __forceinline__ void angle_weight_f32(float v, float S, float invS, bool alg, float &z, float &m2)
+{
+    if (alg) {
+        const float w = v * invS;
+        const float at = atan_pos_f32(fabsf(w));
+        z = 1.5707963267948966f - copysignf(at, w);
+        m2 = fmaf(v, v, S * S) * invS;
+    } else {
+        const float e = ex2_approx(-v * invS * 1.4426950408889634f);  // exp(-v/S)
+        z = 2.0f * atan_pos_f32(e);
+        m2 = 0.5f * S * (rcp_approx(e) + e);
+    }
+}
+
+// FP32 weights: t_a = (s - x) 2/w + a 2/w, psi = 2^(beta log2(e) (sqrt(1 - t^2) - 1)), with the
+// square root as (1 - t^2) rsqrt(1 - t^2); both approximations are good to a few 1e-7.
+template <int W>
+__device__ __forceinline__ void axis_weights_f32(const SpreadArgs &p, float x, float *wt, int *idx)
+{
+    const int s = (int)floorf(x - 0.5f * W) + 1;
+    const float h2 = 2.0f / W;
+    const float t0 = ((float)s - x) * h2;
+    const float bl = (float)(p.beta * 1.4426950408889634);
+    const bool simple = p.simple_fold != 0;
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+        const float t = t0 + (float)a * h2;
+        const float om = fmaf(-t, t, 1.0f);
+        const float e = fmaf(bl, om * rsqrt_approx(om), -bl);
+        wt[a] = om > 0.0f ? ex2_approx(e) : 0.0f;
         idx[a] = fold_cell(s + a, p.n, simple);
     }
 }
@@ -200,6 +285,13 @@ struct SplitTile {  // FP32 path: 64-bit fixed point as (lo, hi) 32-bit words
     unsigned *lo;
     int *hi;
     __device__ __forceinline__ void add(int c, float x) const { add_contrib(lo, hi, c, x); }
+    // 0 <= x < 2^31 known for the whole pair: the high word only takes carries
+    __device__ __forceinline__ void add_small(int c, float x) const
+    {
+        const unsigned v = (unsigned)__float2int_rn(x);
+        const unsigned old = atomicAdd(lo + c, v);
+        if (old + v < old) atomicAdd(hi + c, 1);
+    }
 };
 struct DoubleTile {  // FP64 path: FP64 partial sums
     double *v;
@@ -207,11 +299,14 @@ struct DoubleTile {  // FP64 path: FP64 partial sums
     {
         if (x != 0.0) atomicAdd(v + c, x);
     }
+    __device__ __forceinline__ void add_small(int c, double x) const { add(c, x); }
 };
 
-template <typename T, int D, int W, typename Tile>
-__device__ __forceinline__ void spread_pair(const SpreadArgs &p, const PairData<T, D> &P, T sc, const Tile &tile,
-                                            int row_lo, int nrows, int plane)
+// The M points of one pair.  SMALL: every contribution of the pair is known to lie in
+// [0, 2^31) tile units, so the tile's cheaper add_small applies.
+template <typename T, int D, int W, typename Tile, bool SMALL>
+__device__ __forceinline__ void spread_points(const SpreadArgs &p, const PairData<T, D> &P, T sc, const Tile &tile,
+                                              int row_lo, int nrows, int plane)
 {
     const T *sig = static_cast<const T *>(p.sig);
     const T *wsig = static_cast<const T *>(p.wsig);
@@ -227,7 +322,9 @@ __device__ __forceinline__ void spread_pair(const SpreadArgs &p, const PairData<
         for (int l = 0; l < D; ++l) {
             const T vp = P.cen[l] + P.rad * sig[m * D + l];
             T z, m2;
-            if (alg) {
+            if constexpr (sizeof(T) == 4) {
+                angle_weight_f32(vp, S, invS, alg, z, m2);
+            } else if (alg) {
                 z = Fn<T>::atan2_(S, vp);
                 m2 = (SS + vp * vp) * invS;
             } else {
@@ -258,7 +355,10 @@ __device__ __forceinline__ void spread_pair(const SpreadArgs &p, const PairData<
                 if ((unsigned)r0[a] >= (unsigned)nrows) continue;
                 const int row = r0[a] * plane;
 #pragma unroll
-                for (int b = 0; b < W; ++b) tile.add(row + c1[b], w0[a] * w1[b]);
+                for (int b = 0; b < W; ++b) {
+                    if constexpr (SMALL) tile.add_small(row + c1[b], w0[a] * w1[b]);
+                    else tile.add(row + c1[b], w0[a] * w1[b]);
+                }
             }
         } else {
             T w2[W];
@@ -274,11 +374,29 @@ __device__ __forceinline__ void spread_pair(const SpreadArgs &p, const PairData<
                     const T wab = w0[a] * w1[b];
                     const int line = row + c1[b];
 #pragma unroll
-                    for (int c = 0; c < W; ++c) tile.add(line + c2[c], wab * w2[c]);
+                    for (int c = 0; c < W; ++c) {
+                        if constexpr (SMALL) tile.add_small(line + c2[c], wab * w2[c]);
+                        else tile.add(line + c2[c], wab * w2[c]);
+                    }
                 }
             }
         }
     }
+}
+
+// Spread the M points of one pair into the block tile; `sc` converts to tile units.  Pairs
+// with a non-negative strength whose bound (in tile units) is below 2^30 take the SMALL path.
+template <typename T, int D, int W, typename Tile>
+__device__ __forceinline__ void spread_pair(const SpreadArgs &p, const PairData<T, D> &P, T sc, const Tile &tile,
+                                            int row_lo, int nrows, int plane)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (P.base >= T(0) && pair_bound<T, D>(p, P) * sc < T(1073741824.0f)) {
+            spread_points<T, D, W, Tile, true>(p, P, sc, tile, row_lo, nrows, plane);
+            return;
+        }
+    }
+    spread_points<T, D, W, Tile, false>(p, P, sc, tile, row_lo, nrows, plane);
 }
 
 struct SlabGeom {
