@@ -96,6 +96,7 @@ typedef struct {
     int proj_nodes;
     int launches_per_collide; /* kernels + memsets enqueued by one pg_boltz_collide          */
     size_t device_bytes;   /* device memory owned by the plan                               */
+    int kernels_per_collide; /* kernel launches (memsets excluded) of one collide              */
 } pg_boltz_info_t;
 
 /*
@@ -120,6 +121,28 @@ int pg_boltz_set_stream(pg_boltz_plan_t *plan, void *cuda_stream);
  * next call on the same plan, so calls on one plan must not overlap in time.
  */
 int pg_boltz_collide(pg_boltz_plan_t *plan, const double *f_dev, double *Q_dev);
+
+/*
+ * Time integration of the Petrov-Galerkin ODE system df~_k/dt = Q_k (Eq. spectral_ODE) with
+ * the classical fourth-order Runge-Kutta method (the paper's choice, Section 5.1.2 uses
+ * dt = 0.02): nsteps steps of size dt applied to f_dev in place ((N+1)^d doubles, device).
+ * FP64 state and updates; the evaluations use the plan's precision.  The first call for a
+ * given (f_dev, dt) captures one step (four evaluations and the updates) into a CUDA graph,
+ * later calls replay it.  Asynchronous on the plan's stream.  Not for batched plans.
+ */
+int pg_boltz_rk4(pg_boltz_plan_t *plan, double *f_dev, double dt, int nsteps);
+
+/*
+ * Conservation of the discrete operator in weak form (Eq. weak and Eq. consv, with the
+ * quadrature of Section 4), in FP64 on the device, for the coefficients f_dev:
+ *   out_host[2t]   = sum_{i,j,m} qbar [phi_t(v') - phi_t(v_i)],
+ *   out_host[2t+1] = sum_{i,j,m} qbar (|phi_t(v')| + |phi_t(v_i)|)   (a scale for [2t]),
+ * phi_0 = 1, phi_1..phi_d = v_1..v_d, phi_{d+1} = |v|^2; out_host holds 2(d+2) doubles.  Mass is
+ * conserved exactly; momentum and energy when the sphere set is antipodal.  Overwrites the
+ * plan's reconstruction buffers (so pg_boltz_moments refers to no collide afterwards only if
+ * none follows).  Synchronises the plan's stream.
+ */
+int pg_boltz_conservation(pg_boltz_plan_t *plan, const double *f_dev, double *out_host);
 
 /*
  * FP64 diagnostics of the last pg_boltz_collide, copied to host (synchronises the

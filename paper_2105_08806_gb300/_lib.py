@@ -25,7 +25,7 @@ EXPORTS = (
     "pg_boltz_destroy", "pg_boltz_last_error", "pg_boltz_debug_fail_alloc", "pg_boltz_set_timing",
     "pg_boltz_stage_times", "pg_boltz_project_noalloc", "pg_boltz_probe_shared_atomics",
     "pg_boltz_plan_batched", "pg_boltz_plan_batched_ex", "pg_boltz_collide_batched", "pg_boltz_batched_offsets",
-    "pg_boltz_batched_use_graph",
+    "pg_boltz_batched_use_graph", "pg_boltz_rk4", "pg_boltz_conservation",
 )
 
 
@@ -51,7 +51,7 @@ class Info(ctypes.Structure):
         ("spread_smem_bytes", ctypes.c_size_t),
         ("points", ctypes.c_longlong), ("pairs", ctypes.c_longlong),
         ("proj_nodes", ctypes.c_int), ("launches_per_collide", ctypes.c_int),
-        ("device_bytes", ctypes.c_size_t),
+        ("device_bytes", ctypes.c_size_t), ("kernels_per_collide", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -98,6 +98,10 @@ def lib():
     L.pg_boltz_batched_offsets.restype = ctypes.c_int
     L.pg_boltz_batched_use_graph.argtypes = [vp, ctypes.c_int]
     L.pg_boltz_batched_use_graph.restype = ctypes.c_int
+    L.pg_boltz_conservation.argtypes = [vp, vp, dp]
+    L.pg_boltz_conservation.restype = ctypes.c_int
+    L.pg_boltz_rk4.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int]
+    L.pg_boltz_rk4.restype = ctypes.c_int
     L.pg_boltz_probe_shared_atomics.argtypes = [vp, dp]
     L.pg_boltz_probe_shared_atomics.restype = ctypes.c_int
     L.pg_boltz_set_timing.argtypes = [vp, ctypes.c_int]
@@ -162,6 +166,18 @@ class Plan:
 
     def collide(self, f, Q):
         _check(lib().pg_boltz_collide(self._h, ctypes.c_void_p(_ptr(f)), ctypes.c_void_p(_ptr(Q))))
+
+    def conservation(self, f):
+        """Weak-form (value, scale) pairs for phi = 1, v_1..v_d, |v|^2 of the coefficients f."""
+        n = 2 * (self.d + 2)
+        out = (ctypes.c_double * n)()
+        _check(lib().pg_boltz_conservation(self._h, ctypes.c_void_p(_ptr(f)), out))
+        vals = list(out)
+        return [(vals[2 * t], vals[2 * t + 1]) for t in range(self.d + 2)]
+
+    def rk4(self, f, dt, nsteps):
+        """nsteps classical RK4 steps of df/dt = Q(f) applied to f (device, in place)."""
+        _check(lib().pg_boltz_rk4(self._h, ctypes.c_void_p(_ptr(f)), float(dt), int(nsteps)))
 
     def moments(self):
         out = (ctypes.c_double * 6)()

@@ -287,6 +287,7 @@ __device__ __forceinline__ void cell_args(const BatchArgs &b, const CellDesc &cd
     sa.sig = f32 ? (const void *)(b.sig32 + cd.sig_off * b.d) : (const void *)(b.sig64 + cd.sig_off * b.d);
     sa.wsig = f32 ? (const void *)(b.wsig32 + cd.sig_off) : (const void *)(b.wsig64 + cd.sig_off);
     sa.Wsig = cd.Wsig;
+    sa.wmax_frac = 1.0 / cd.M;  // the sphere sets have equal weights
     sa.bound = nullptr;
     sa.tau = nullptr;  // the batched kernel reads Tcell directly
     sa.grid = b.grid + cd.grid_off;
@@ -778,7 +779,8 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
     in.spread_smem_bytes = B->spread_smem;
     in.points = B->points;
     in.pairs = B->pairs;
-    in.launches_per_collide = 5;
+    in.launches_per_collide = 4;
+    in.kernels_per_collide = 3;
     in.device_bytes = p->device_bytes;
     p->d = d;
     p->prec = B->prec;

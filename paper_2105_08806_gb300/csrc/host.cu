@@ -243,6 +243,9 @@ void free_plan(pg_boltz_plan_t *p)
     for (cudaEvent_t &e : p->ev)
         if (e) cudaEventDestroy(e);
     if (p->batch) pg_free_batch(p->batch);
+    if (p->rk_exec) cudaGraphExecDestroy(p->rk_exec);
+    if (p->rk_graph) cudaGraphDestroy(p->rk_graph);
+    if (p->rk_cap_stream) cudaStreamDestroy(p->rk_cap_stream);
     for (void *q : p->allocs) cudaFree(q);
     p->allocs.clear();
     delete p;

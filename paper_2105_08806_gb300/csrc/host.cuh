@@ -125,6 +125,13 @@ struct pg_boltz_plan_s {
     double *tau = nullptr;     // scalar screening threshold (follows the bound)
     unsigned long long *hist = nullptr;  // screening histogram (follows tau)
     double screen_eps = 0.0;   // skipped strength budget relative to B (0: no screening)
+    // RK4 time stepping: stage slopes k1..k4 and the stage argument, (N+1)^d each
+    double *rk = nullptr;
+    cudaStream_t rk_cap_stream = nullptr;
+    cudaGraph_t rk_graph = nullptr;
+    cudaGraphExec_t rk_exec = nullptr;
+    double *rk_f = nullptr;
+    double rk_dt = 0.0;
     BatchState *batch = nullptr;  // non-null for batched plans
 };
 

@@ -28,6 +28,7 @@ struct SpreadArgs {
     const void *sig;      // M x d sphere points
     const void *wsig;     // M sphere weights
     double Wsig;          // sum_m w_m
+    double wmax_frac;     // max_m w_m / sum_m w_m: one point's share of a pair's strength bound
     const double *bound;  // device scalar B >= sum_p |q_p| (written by the loss kernel)
     const double *tau;    // device scalar: node pairs whose strength bound is below it are skipped (0: none)
     unsigned long long *grid;  // nf^d folded grid, int64 fixed point in units of 2^-Eg
@@ -101,6 +102,14 @@ cudaError_t launch_axis_pass_fixed(const unsigned long long *in, Dims3 in_dims, 
 cudaError_t launch_final(const double *G, Dims3 g_dims, const double *D, const double *H,
                          Dims3 h_dims, const double *E, int m, double *Q, double *Qplus,
                          double *Qcopy, cudaStream_t s);
+// RK stage argument y = x + c k, and the RK4 update f += dt/6 (k1 + 2k2 + 2k3 + k4).
+cudaError_t launch_axpy(const double *x, const double *k, double c, double *y, long long n, cudaStream_t s);
+cudaError_t launch_rk4_update(double *f, const double *k1, const double *k2, const double *k3, const double *k4,
+                              double dt, long long n, cudaStream_t s);
+// Discrete weak-form functionals and scales for phi in {1, v_l, |v|^2}, added into out[2(d+2)].
+cudaError_t launch_weak_moments(const double *a, const double *vnode, int N, int d, int M, const double *sig,
+                                const double *wsig, double gamma, int fast_gamma, double Bconst, double *out,
+                                cudaStream_t s);
 // Diagnostics: mass/energy functionals of Q and Qplus and their L2 norms into out[6].
 cudaError_t launch_moments(const double *Q, const double *Qplus, int d, int N, double S,
                            double *out, cudaStream_t s);

@@ -92,7 +92,8 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
         (rc = dev_alloc(p, (void **)&p->grid, grid_cells * 8 + 16 + pgb::kScreenBins * 8)) ||
         (rc = dev_alloc(p, (void **)&p->ub, (size_t)p->nnode * 8)) ||
         (rc = dev_alloc(p, (void **)&p->Qplus, modes * 8)) || (rc = dev_alloc(p, (void **)&p->Qlast, modes * 8)) ||
-        (rc = dev_alloc(p, (void **)&p->mom, 8 * 8)))
+        (rc = dev_alloc(p, (void **)&p->rk, 5 * modes * 8)) ||
+        (rc = dev_alloc(p, (void **)&p->mom, 16 * 8)))
         return rc;
     // one allocation: [grid | B | tau | screening histogram], cleared by one memset per call
     p->bound = reinterpret_cast<double *>(p->grid + grid_cells);
@@ -157,6 +158,7 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
     ka.sig = f32 ? (const void *)p->sig32 : (const void *)p->sig64;
     ka.wsig = f32 ? (const void *)p->wsig32 : (const void *)p->wsig64;
     ka.Wsig = p->Wsig;
+    ka.wmax_frac = *std::max_element(sw.begin(), sw.end()) / p->Wsig;
     ka.bound = p->bound;
     ka.tau = p->tau;
     ka.grid = p->grid;
@@ -263,6 +265,7 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_ex(const pg_boltz_opts_t *opts)
     in.points = p->npairs * p->M;
     in.proj_nodes = p->Mp;
     in.launches_per_collide = 3 + 3 * p->d;
+    in.kernels_per_collide = 2 + 3 * p->d;
     in.device_bytes = p->device_bytes;
     return p;
 }
@@ -371,7 +374,104 @@ PG_API int pg_boltz_collide(pg_boltz_plan_t *p, const double *f_dev, double *Q_d
     p->ev_recorded = p->timing;
     p->last_launches = launches;
     p->info.launches_per_collide = launches;
+    p->info.kernels_per_collide = launches - 1;  // one memset
     p->have_q = true;
+    return PG_OK;
+}
+
+namespace {
+
+// One RK4 step of df~/dt = Q(f~) on stream s: four evaluations and the update.
+int rk4_step(pg_boltz_plan_t *p, double *f, double dt, cudaStream_t s)
+{
+    const long long n = (long long)ipow(p->N + 1, p->d);
+    double *k1 = p->rk, *k2 = k1 + n, *k3 = k2 + n, *k4 = k3 + n, *y = k4 + n;
+    cudaStream_t keep = p->stream;
+    const bool timing = p->timing;
+    p->stream = s;
+    p->timing = false;
+    int rc = pg_boltz_collide(p, f, k1);
+    if (!rc) rc = cuda_check(pgb::launch_axpy(f, k1, 0.5 * dt, y, n, s), "rk4 stage");
+    if (!rc) rc = pg_boltz_collide(p, y, k2);
+    if (!rc) rc = cuda_check(pgb::launch_axpy(f, k2, 0.5 * dt, y, n, s), "rk4 stage");
+    if (!rc) rc = pg_boltz_collide(p, y, k3);
+    if (!rc) rc = cuda_check(pgb::launch_axpy(f, k3, dt, y, n, s), "rk4 stage");
+    if (!rc) rc = pg_boltz_collide(p, y, k4);
+    if (!rc) rc = cuda_check(pgb::launch_rk4_update(f, k1, k2, k3, k4, dt, n, s), "rk4 update");
+    p->stream = keep;
+    p->timing = timing;
+    return rc;
+}
+
+}  // namespace
+
+PG_API int pg_boltz_rk4(pg_boltz_plan_t *p, double *f_dev, double dt, int nsteps)
+{
+    if (!p) return set_error(PG_ERR_ARG, "plan is NULL");
+    if (p->batch) return set_error(PG_ERR_STATE, "RK4 stepping takes a single plan");
+    if (!f_dev || nsteps < 0 || !std::isfinite(dt)) return set_error(PG_ERR_ARG, "bad f, dt or nsteps");
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return set_error(PG_ERR_CUDA, "cannot select the plan's device");
+    int rc;
+    if (!p->rk_exec || p->rk_f != f_dev || p->rk_dt != dt) {
+        // capture one step once per (f, dt), then replay it
+        if (p->rk_exec) {
+            cudaGraphExecDestroy(p->rk_exec);
+            p->rk_exec = nullptr;
+        }
+        if (p->rk_graph) {
+            cudaGraphDestroy(p->rk_graph);
+            p->rk_graph = nullptr;
+        }
+        if (!p->rk_cap_stream &&
+            (rc = cuda_check(cudaStreamCreateWithFlags(&p->rk_cap_stream, cudaStreamNonBlocking), "capture stream")))
+            return rc;
+        if ((rc = cuda_check(cudaStreamBeginCapture(p->rk_cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture")))
+            return rc;
+        rc = rk4_step(p, f_dev, dt, p->rk_cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(p->rk_cap_stream, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if ((rc = cuda_check(e, "end capture"))) return rc;
+        p->rk_graph = g;
+        if ((rc = cuda_check(cudaGraphInstantiate(&p->rk_exec, p->rk_graph, 0), "graph instantiate"))) return rc;
+        p->rk_f = f_dev;
+        p->rk_dt = dt;
+    }
+    for (int s = 0; s < nsteps; ++s)
+        if ((rc = cuda_check(cudaGraphLaunch(p->rk_exec, p->stream), "graph launch"))) return rc;
+    return PG_OK;
+}
+
+PG_API int pg_boltz_conservation(pg_boltz_plan_t *p, const double *f_dev, double *out_host)
+{
+    if (!p || !f_dev || !out_host) return set_error(PG_ERR_ARG, "NULL argument");
+    if (p->batch) return set_error(PG_ERR_STATE, "conservation diagnostics take a single plan");
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return set_error(PG_ERR_CUDA, "cannot select the plan's device");
+    const int d = p->d, N = p->N;
+    int launches = 0, rc;
+    pgb::Dims3 dims = dims_of(d, N + 1, N + 1, N + 1);
+    const double *cur = nullptr;
+    if ((rc = leading_passes(p, f_dev, dims, p->R, N, p->tA, p->tB, &cur, &launches))) return rc;
+    if ((rc = cuda_check(pgb::launch_recon_last(cur, dims, p->R, N, p->scale_a, d, p->a64, nullptr, p->stream),
+                         "reconstruct")))
+        return rc;
+    const int nout = 2 * (d + 2);
+    if ((rc = cuda_check(cudaMemsetAsync(p->mom, 0, nout * sizeof(double), p->stream), "memset"))) return rc;
+    if ((rc = cuda_check(pgb::launch_weak_moments(p->a64, p->v64, N, d, p->M, p->sig64, p->wsig64, p->gamma,
+                                                  p->fast_gamma, p->Bconst, p->mom, p->stream),
+                         "weak moments")))
+        return rc;
+    double tmp[10];
+    if ((rc = cuda_check(cudaMemcpyAsync(tmp, p->mom, nout * sizeof(double), cudaMemcpyDeviceToHost, p->stream),
+                         "copy")))
+        return rc;
+    if ((rc = cuda_check(cudaStreamSynchronize(p->stream), "sync"))) return rc;
+    std::memcpy(out_host, tmp, nout * sizeof(double));
     return PG_OK;
 }
 

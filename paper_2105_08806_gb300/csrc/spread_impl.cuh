@@ -285,12 +285,14 @@ struct SplitTile {  // FP32 path: 64-bit fixed point as (lo, hi) 32-bit words
     unsigned *lo;
     int *hi;
     __device__ __forceinline__ void add(int c, float x) const { add_contrib(lo, hi, c, x); }
-    // 0 <= x < 2^31 known for the whole pair: the high word only takes carries
+    // |x| < 2^31 known for the whole pair: the high word takes the sign and the carry, which
+    // cancel for most negative contributions
     __device__ __forceinline__ void add_small(int c, float x) const
     {
-        const unsigned v = (unsigned)__float2int_rn(x);
-        const unsigned old = atomicAdd(lo + c, v);
-        if (old + v < old) atomicAdd(hi + c, 1);
+        const int v = __float2int_rn(x);
+        const unsigned old = atomicAdd(lo + c, (unsigned)v);
+        const int h = (v >> 31) + ((old + (unsigned)v < old) ? 1 : 0);
+        if (h) atomicAdd(hi + c, h);
     }
 };
 struct DoubleTile {  // FP64 path: FP64 partial sums
@@ -303,7 +305,7 @@ struct DoubleTile {  // FP64 path: FP64 partial sums
 };
 
 // The M points of one pair.  SMALL: every contribution of the pair is known to lie in
-// [0, 2^31) tile units, so the tile's cheaper add_small applies.
+// (-2^31, 2^31) tile units, so the tile's cheaper add_small applies.
 template <typename T, int D, int W, typename Tile, bool SMALL>
 __device__ __forceinline__ void spread_points(const SpreadArgs &p, const PairData<T, D> &P, T sc, const Tile &tile,
                                               int row_lo, int nrows, int plane)
@@ -385,13 +387,14 @@ __device__ __forceinline__ void spread_points(const SpreadArgs &p, const PairDat
 }
 
 // Spread the M points of one pair into the block tile; `sc` converts to tile units.  Pairs
-// with a non-negative strength whose bound (in tile units) is below 2^30 take the SMALL path.
+// whose largest single contribution is bounded below 2^30 tile units in magnitude (pair bound
+// x max_m w_m / sum_m w_m, kernel weights <= 1) take the SMALL path.
 template <typename T, int D, int W, typename Tile>
 __device__ __forceinline__ void spread_pair(const SpreadArgs &p, const PairData<T, D> &P, T sc, const Tile &tile,
                                             int row_lo, int nrows, int plane)
 {
     if constexpr (sizeof(T) == 4) {
-        if (P.base >= T(0) && pair_bound<T, D>(p, P) * sc < T(1073741824.0f)) {
+        if (pair_bound<T, D>(p, P) * sc * T(p.wmax_frac) < T(1073741824.0f)) {
             spread_points<T, D, W, Tile, true>(p, P, sc, tile, row_lo, nrows, plane);
             return;
         }

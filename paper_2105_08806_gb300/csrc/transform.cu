@@ -307,6 +307,91 @@ __global__ void k_moments(const double *__restrict__ Q, const double *__restrict
     }
 }
 
+constexpr int kWeakThreads = 256;
+
+// Discrete weak form of the collision operator (Eq. weak with the quadrature of Section 4):
+//   out[2t]   = sum_{i,j,m} qbar [phi_t(v') - phi_t(v_i)],
+//   out[2t+1] = sum_{i,j,m} qbar (|phi_t(v')| + |phi_t(v_i)|),
+// qbar = a_i a_j w_m Bconst |v_i - v_j|^gamma, for phi_t in {1, v_1, .., v_d, |v|^2} (t = 0..d+1).
+// One thread per node pair, FP64 throughout; block sums are added to out with atomics.
+__global__ void __launch_bounds__(kWeakThreads) k_weak_moments(const double *__restrict__ a,
+                                                               const double *__restrict__ vnode, int N, int d,
+                                                               int M, const double *__restrict__ sig,
+                                                               const double *__restrict__ wsig, double gamma,
+                                                               int fast_gamma, double Bconst, double *__restrict__ out)
+{
+    const int nnode = (d == 2) ? N * N : N * N * N;
+    const long long npairs = (long long)nnode * nnode;
+    double acc[10];
+    for (int t = 0; t < 10; ++t) acc[t] = 0.0;
+    for (long long pr = blockIdx.x * (long long)blockDim.x + threadIdx.x; pr < npairs;
+         pr += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(pr / nnode), j = (int)(pr - (long long)i * nnode);
+        const double aij = a[i] * a[j];
+        if (aij == 0.0) continue;
+        double vi[3] = {0, 0, 0}, vj[3] = {0, 0, 0}, g2 = 0.0;
+        int ii = i, jj = j;
+        for (int l = d - 1; l >= 0; --l) {
+            vi[l] = vnode[ii % N];
+            vj[l] = vnode[jj % N];
+            ii /= N;
+            jj /= N;
+            g2 += (vi[l] - vj[l]) * (vi[l] - vj[l]);
+        }
+        const double g = sqrt(g2);
+        double B;
+        switch (fast_gamma) {
+        case 0: B = Bconst; break;
+        case 1: B = Bconst * g; break;
+        case 2: B = Bconst * sqrt(g); break;
+        default: B = (g2 > 0.0) ? Bconst * pow(g, gamma) : 0.0; break;
+        }
+        double vi2 = 0.0;
+        for (int l = 0; l < d; ++l) vi2 += vi[l] * vi[l];
+        for (int m = 0; m < M; ++m) {
+            const double q = aij * B * wsig[m];
+            double vp2 = 0.0;
+            for (int l = 0; l < d; ++l) {
+                const double vp = 0.5 * (vi[l] + vj[l]) + 0.5 * g * sig[m * d + l];
+                vp2 += vp * vp;
+                acc[2 + 2 * l] += q * (vp - vi[l]);
+                acc[3 + 2 * l] += fabs(q) * (fabs(vp) + fabs(vi[l]));
+            }
+            acc[1] += 2.0 * fabs(q);  // phi = 1: the difference is exactly zero
+            acc[2 + 2 * d] += q * (vp2 - vi2);
+            acc[3 + 2 * d] += fabs(q) * (vp2 + vi2);
+        }
+    }
+    __shared__ double part[kWeakThreads / 32][10];
+    for (int t = 0; t < 2 * (d + 2); ++t) {
+        double v = acc[t];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5][t] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * (d + 2)) {
+        double v = 0.0;
+        for (int w = 0; w < kWeakThreads / 32; ++w) v += part[w][threadIdx.x];
+        atomicAdd(out + threadIdx.x, v);
+    }
+}
+
+// y = x + c k (an RK stage argument).
+__global__ void k_axpy(const double *__restrict__ x, const double *__restrict__ k, double c, double *__restrict__ y,
+                       long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = fma(c, k[i], x[i]);
+}
+
+// f += dt/6 (k1 + 2 k2 + 2 k3 + k4) (the classical fourth-order Runge-Kutta update).
+__global__ void k_rk4_update(double *__restrict__ f, const double *__restrict__ k1, const double *__restrict__ k2,
+                             const double *__restrict__ k3, const double *__restrict__ k4, double dt, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        f[i] += (dt / 6.0) * (k1[i] + 2.0 * (k2[i] + k3[i]) + k4[i]);
+}
+
 int grid_for(long long total)
 {
     long long b = (total + kThreads - 1) / kThreads;
@@ -373,6 +458,27 @@ cudaError_t launch_final(const double *G, Dims3 g_dims, const double *D, const d
     k_final<<<grid_for((long long)g_dims.e[0] * g_dims.e[1] * m), kThreads, 0, s>>>(G, g_dims, D, H,
                                                                                    h_dims, E, m, Q,
                                                                                    Qplus, Qcopy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(const double *x, const double *k, double c, double *y, long long n, cudaStream_t s)
+{
+    k_axpy<<<grid_for(n), kThreads, 0, s>>>(x, k, c, y, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rk4_update(double *f, const double *k1, const double *k2, const double *k3, const double *k4,
+                              double dt, long long n, cudaStream_t s)
+{
+    k_rk4_update<<<grid_for(n), kThreads, 0, s>>>(f, k1, k2, k3, k4, dt, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weak_moments(const double *a, const double *vnode, int N, int d, int M, const double *sig,
+                                const double *wsig, double gamma, int fast_gamma, double Bconst, double *out,
+                                cudaStream_t s)
+{
+    k_weak_moments<<<4 * 152, kWeakThreads, 0, s>>>(a, vnode, N, d, M, sig, wsig, gamma, fast_gamma, Bconst, out);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,89 @@
+"""RK4 time stepping of df~/dt = Q(f~) (Eq. spectral_ODE; RK4 with dt = 0.02 as in Section 5.1.2)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2105_08806_gb300 import PG_PREC_FP32, PG_PREC_FP64
+from paper_2105_08806_gb300 import workloads as W
+
+from _helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    from paper_2105_08806_gb300.build import build
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build()
+
+
+def _oracle_rk4(ft, dt, steps, d, N, M, S, gamma, r):
+    Qf = lambda x: O.collide(x, d, N, M, S, gamma, r=r)
+    f = np.array(ft, dtype=np.float64)
+    for _ in range(steps):
+        k1 = Qf(f)
+        k2 = Qf(f + 0.5 * dt * k1)
+        k3 = Qf(f + 0.5 * dt * k2)
+        k4 = Qf(f + dt * k3)
+        f = f + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+    return f
+
+
+def test_rk4_steps_match_oracle():
+    import torch
+    from paper_2105_08806_gb300 import Plan
+    d, N, M, S, gamma, dt = 2, 10, 8, 2.0, 1.0, 0.05
+    ft = O.project(W.c1_2d_maxwell(), d, N, S, 1).ravel()
+    ref = _oracle_rk4(ft, dt, 2, d, N, M, S, gamma, 1)
+    f = torch.as_tensor(ft.copy(), device="cuda")
+    with Plan(d, N, M, S, gamma, 1e-13, precision=PG_PREC_FP64) as plan:
+        plan.rk4(f, dt, 1)
+        plan.rk4(f, dt, 1)  # second call replays the captured step
+        torch.cuda.synchronize()
+    assert rel_l2(f.cpu().numpy() - ft, ref - ft) < 1e-9
+
+
+def _moments(ft, N, S, r, Mq=240):
+    """P_ij = int f_N v_i v_j, q_i = int f_N v_i |v|^2 by Chebyshev-Gauss quadrature in xi
+    (dv = omega(xi)/mu(xi)^2 dxi per axis, Eq. 1D_mapping)."""
+    xi, v, w = O.projection_nodes(Mq, S, r)
+    wv = w / O.mu_of_xi(xi, S, r) ** 2
+    V1, V2 = np.meshgrid(v, v, indexing="ij")
+    pts = np.stack([V1.ravel(), V2.ravel()], 1)
+    fv = O.fN_values(ft, 2, N, S, r, pts).reshape(Mq, Mq) * np.outer(wv, wv)
+    v2 = V1 ** 2 + V2 ** 2
+    return np.array([np.sum(fv * V1 * V1), np.sum(fv * V1 * V2), np.sum(fv * V2 * V2),
+                     np.sum(fv * V1 * v2), np.sum(fv * V2 * v2)])
+
+
+def test_two_maxwellian_moments_follow_closed_forms():
+    """Section 5.1.2: f0 = two Maxwellians (rho = 1/2, T = 1, V1 = (-1,2), V2 = (3,-3)), B = 1/(2 pi),
+    logarithmic map, S from v(xi_2) = -L with L = 14.35, M_v = N + 2, M_sigma = N, RK4 with
+    dt = 0.02 to t = 1; moments against the paper's exact P_ij(t), q_i(t)."""
+    import torch
+    from paper_2105_08806_gb300 import Plan
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "moments2d_closed_form.txt")) if l[0] != "#"]
+    A = np.array([float(x[4]) for x in rows])
+    C = np.array([float(x[5]) for x in rows])
+    N, L, dt, T = 32, 14.35, 0.02, 1.0
+    S = L / math.atanh(math.cos(math.pi / (N + 1)))
+    f0 = lambda p: W.maxwellian(p, 0.5, [-1, 2], 1.0) + W.maxwellian(p, 0.5, [3, -3], 1.0)
+    ft = O.project(f0, 2, N, S, 0).ravel()
+    m0 = _moments(ft, N, S, 0)
+    assert np.abs(m0 - (A + C)).max() < 1e-3  # projection of the initial datum
+    f = torch.as_tensor(ft, device="cuda")
+    with Plan(2, N, N, S, 0.0, 1e-7, precision=PG_PREC_FP32, map_log=True) as plan:
+        plan.rk4(f, dt, int(round(T / dt)))
+        torch.cuda.synchronize()
+    m1 = _moments(f.cpu().numpy(), N, S, 0)
+    exact = A * math.exp(-T / 2) + C
+    assert np.abs(m1 - exact).max() < 2e-3, (m1, exact)
+    # the moments did change: the test is not passed by a frozen f
+    assert np.abs(m1 - m0).max() > 0.3
