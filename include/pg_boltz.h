@@ -91,8 +91,10 @@ typedef struct {
     int slabs;             /* shared-memory slabs of the folded grid along axis 1           */
     int spread_blocks, spread_threads;
     size_t spread_smem_bytes;
-    long long points;      /* non-uniform points per evaluation, M N^(2d)                   */
-    long long pairs;       /* node pairs per evaluation, N^(2d)                             */
+    long long points;      /* non-uniform points spread per evaluation, M x pairs            */
+    long long pairs;       /* node pairs spread per evaluation: each unordered pair {i, j} of
+                              the N^d interior nodes once, N^d (N^d + 1) / 2 (the orders (i, j)
+                              and (j, i) add the same points with the same strength)          */
     int proj_nodes;
     int launches_per_collide; /* kernels + memsets enqueued by one pg_boltz_collide          */
     size_t device_bytes;   /* device memory owned by the plan                               */
@@ -183,6 +185,20 @@ int pg_boltz_project_nodes(const pg_boltz_plan_t *plan, double *v_host, int *cou
  * nodes (C order); ftilde_dev: device array of (N+1)^d doubles.  Asynchronous.
  */
 int pg_boltz_project(pg_boltz_plan_t *plan, const double *fvals_dev, double *ftilde_dev);
+
+/*
+ * Inverse transform at arbitrary velocities: u_N(v) = sum_k u~_k prod_l T~_{k_l}(v_l) with the
+ * trial functions T~_k = mu^4 T_k(xi(v)) / sqrt(c_k) of the plan's map and S (Eq. fN_Expansion,
+ * Eq. 1DCheby).  Applied to f~ it gives f_N(v); applied to the Q_k of pg_boltz_collide it gives
+ * Q_N(v), the trial-space function with those weak-form coefficients.
+ * coef_dev: device array of (N+1)^d doubles (C order, the layout of pg_boltz_collide);
+ * pts_dev: device array of npts x d doubles (row-major, one velocity per row, any finite value);
+ * out_dev: device array of npts doubles.  Caller owns all three.  npts = 0 is a no-op.
+ * Asynchronous on the plan's stream.  PG_ERR_ARG for npts < 0 or NULL pointers,
+ * PG_ERR_STATE on batched plans.
+ */
+int pg_boltz_evaluate(pg_boltz_plan_t *plan, const double *coef_dev, long long npts, const double *pts_dev,
+                      double *out_dev);
 
 /* Describe the plan (host-only). */
 int pg_boltz_info(const pg_boltz_plan_t *plan, pg_boltz_info_t *out);

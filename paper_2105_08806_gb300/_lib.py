@@ -25,7 +25,7 @@ EXPORTS = (
     "pg_boltz_destroy", "pg_boltz_last_error", "pg_boltz_debug_fail_alloc", "pg_boltz_set_timing",
     "pg_boltz_stage_times", "pg_boltz_project_noalloc", "pg_boltz_probe_shared_atomics",
     "pg_boltz_plan_batched", "pg_boltz_plan_batched_ex", "pg_boltz_collide_batched", "pg_boltz_batched_offsets",
-    "pg_boltz_batched_use_graph", "pg_boltz_rk4", "pg_boltz_conservation",
+    "pg_boltz_batched_use_graph", "pg_boltz_rk4", "pg_boltz_conservation", "pg_boltz_evaluate",
 )
 
 
@@ -81,6 +81,7 @@ def lib():
     L.pg_boltz_moments.argtypes = [vp, dp]
     L.pg_boltz_project_nodes.argtypes = [vp, dp, ip]
     L.pg_boltz_project.argtypes = [vp, vp, vp]
+    L.pg_boltz_evaluate.argtypes = [vp, vp, ctypes.c_longlong, vp, vp]
     L.pg_boltz_info.argtypes = [vp, ctypes.POINTER(Info)]
     L.pg_boltz_destroy.argtypes = [vp]
     L.pg_boltz_destroy.restype = None
@@ -203,6 +204,14 @@ class Plan:
 
     def project(self, fvals, ftilde):
         _check(lib().pg_boltz_project(self._h, ctypes.c_void_p(_ptr(fvals)), ctypes.c_void_p(_ptr(ftilde))))
+
+    def evaluate(self, coef, pts, out):
+        """u_N at the npts rows of pts (npts x d float64 CUDA tensor) into out (npts float64)."""
+        npts = pts.numel() // self.d
+        if pts.numel() != npts * self.d or out.numel() < npts or coef.numel() < (self.N + 1) ** self.d:
+            raise ValueError("pts must hold npts x d values, out npts, coef (N+1)^d")
+        _check(lib().pg_boltz_evaluate(self._h, ctypes.c_void_p(_ptr(coef)), npts,
+                                       ctypes.c_void_p(_ptr(pts)), ctypes.c_void_p(_ptr(out))))
 
     def info(self) -> dict:
         inf = Info()

@@ -32,7 +32,7 @@ namespace pgb {
 struct CellDesc {
     int N, M, nf, n, nnode, fast_gamma;
     double S, gamma, Wsig;
-    long long pairs;     // nnode^2
+    long long pairs;     // unordered node pairs, nnode (nnode + 1) / 2
     long long f_off;     // packed modes (f~ and Q)
     long long a_off;     // packed node values (a, h)
     long long grid_off;  // packed folded grids
@@ -363,6 +363,7 @@ __global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __gr
             PairData<T, D> P;
             if (!load_pair<T, D>(sa, pr, P)) continue;
             if (tau > T(0) && pair_bound<T, D>(sa, P) < tau) continue;
+            P.base *= P.mult;
             if constexpr (F32) {
                 spread_pair<T, D, W>(sa, P, sc, SplitTile{lo, hi}, 0, s_cd.nf, plane);
             } else {
@@ -632,7 +633,7 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
         cd.fast_gamma = (gammas[c] == 0.0) ? 0 : (gammas[c] == 1.0) ? 1 : (gammas[c] == 0.5) ? 2 : 3;
         cd.S = Ss[c];
         cd.gamma = gammas[c];
-        cd.pairs = (long long)cd.nnode * cd.nnode;
+        cd.pairs = pgb::unordered_pairs(cd.nnode);
         auto nk = std::make_pair(N, Ss[c]);
         if (!node_key.count(nk)) {
             NodeTables nt = node_tables(N, Ss[c], B->r);

@@ -15,7 +15,7 @@ namespace pgb {
 struct SpreadArgs {
     int d, N, M, r;
     int nnode;            // N^d interior nodes
-    long long npairs;     // nnode^2 (i, j) pairs
+    long long npairs;     // unordered node pairs, unordered_pairs(nnode)
     int n, nf;            // periodic grid size, folded cells per axis (n/2 + 1)
     int rows_per_slab;    // folded-grid rows (axis 0) held in shared memory by one block
     int nslab;            // number of slabs covering axis 0
@@ -34,6 +34,17 @@ struct SpreadArgs {
     unsigned long long *grid;  // nf^d folded grid, int64 fixed point in units of 2^-Eg
     int simple_fold;      // 1 when w <= n/2: unfolded indices lie in [-n/2, n] (no modulo needed)
 };
+
+// Node pairs the spreading kernels walk: each unordered pair {i, j} once (the two orders add the
+// same points with the same strength), nnode (nnode + 1) / 2 in all.
+__host__ __device__ inline long long unordered_pairs(long long nnode) { return nnode * (nnode + 1) / 2; }
+
+// Shared memory of the warp point queues of a slabbed spreading block of `threads` threads:
+// 32 points per warp, d coordinates and a strength of `elem` bytes each.
+__host__ __device__ inline size_t spread_queue_bytes(int threads, int d, size_t elem)
+{
+    return (size_t)(threads / 32) * 32 * (d + 1) * elem;
+}
 
 // Exponent Eg of the grid's fixed-point unit 2^-Eg: the largest E with B 2^E < 2^61 for the
 // bound B >= sum_p |q_p| (0 when B is zero or not finite).

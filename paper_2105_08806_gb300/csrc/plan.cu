@@ -31,7 +31,7 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
 {
     const int d = p->d, N = p->N, M = p->M;
     p->nnode = (d == 2) ? N * N : N * N * N;
-    p->npairs = (long long)p->nnode * p->nnode;
+    p->npairs = pgb::unordered_pairs(p->nnode);
     p->fast_gamma = (p->gamma == 0.0) ? 0 : (p->gamma == 1.0) ? 1 : (p->gamma == 0.5) ? 2 : 3;
     p->Bconst = 1.0 / (d == 2 ? 2.0 * kPi : 4.0 * kPi);
 
@@ -107,13 +107,22 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
     const size_t elem = 8;  // two 32-bit words per cell (64-bit fixed point), both precisions
     const size_t plane = (size_t)nfd1;
     const size_t max_smem = prop.sharedMemPerBlockOptin - 1024;  // leave room for the kernels' static shared memory
+    const bool f32 = (p->prec == PG_PREC_FP32);
+    const int max_threads = f32 ? pgb::kMaxThreadsF32 : pgb::kMaxThreadsF64;
     int rows_fit = (int)std::min<size_t>(p->nf, max_smem / (plane * elem));
+    size_t qbytes = 0;
+    if (rows_fit < p->nf) {
+        // slabbed grid: the warps' point queues (one block per SM, max_threads threads unless
+        // set) share the block's shared memory with the slab
+        const int thr = (o.spread_threads > 0) ? o.spread_threads : max_threads;
+        qbytes = pgb::spread_queue_bytes(thr, d, f32 ? 4 : 8);
+        rows_fit = (max_smem > qbytes) ? (int)std::min<size_t>(p->nf, (max_smem - qbytes) / (plane * elem)) : 0;
+    }
     if (rows_fit < 1) return set_error(PG_ERR_ARG, "folded grid plane of %zu cells does not fit shared memory", plane);
     p->nslab = (p->nf + rows_fit - 1) / rows_fit;
     p->rows_per_slab = (p->nf + p->nslab - 1) / p->nslab;
     p->nslab = (p->nf + p->rows_per_slab - 1) / p->rows_per_slab;  // no empty trailing slab
-    p->spread_smem = (size_t)p->rows_per_slab * plane * elem;
-    const int max_threads = (p->prec == PG_PREC_FP32) ? pgb::kMaxThreadsF32 : pgb::kMaxThreadsF64;
+    p->spread_smem = (size_t)p->rows_per_slab * plane * elem + (p->nslab > 1 ? qbytes : 0);
     int per_sm = (int)(prop.sharedMemPerMultiprocessor / (p->spread_smem + 1024 + prop.reservedSharedMemPerBlock));
     per_sm = std::max(per_sm, 1);
     if (o.spread_threads > 0) {
@@ -123,8 +132,11 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
         int t = (1024 / per_sm) / 32 * 32;
         p->spread_threads = std::max(128, std::min(max_threads, t));
     }
+    if (p->nslab > 1 && o.spread_threads <= 0) p->spread_threads = max_threads;  // the queues were sized for it
     if (p->spread_threads % 32 || p->spread_threads > max_threads)
         return set_error(PG_ERR_ARG, "spread_threads must be a multiple of 32 and <= %d", max_threads);
+    if (p->nslab > 1 && pgb::spread_queue_bytes(p->spread_threads, d, f32 ? 4 : 8) > qbytes)
+        return set_error(PG_ERR_STATE, "internal: point queues larger than reserved");
     per_sm = std::min(per_sm, prop.maxThreadsPerMultiProcessor / p->spread_threads);
     if (o.spread_blocks_per_sm > 0) per_sm = std::min(per_sm, o.spread_blocks_per_sm);
     per_sm = std::max(per_sm, 1);
@@ -136,7 +148,6 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
 
     // ---- spreading-kernel arguments
     pgb::SpreadArgs &ka = p->sargs;
-    const bool f32 = (p->prec == PG_PREC_FP32);
     ka.d = d;
     ka.N = N;
     ka.M = M;

@@ -227,15 +227,26 @@ struct PairData {
     T cen[D];  // (v_i + v_j)/2
     T rad;     // |v_i - v_j|/2
     T base;    // a_i a_j B(|v_i - v_j|)
+    T mult;    // 2 for i != j (the pair stands for (i, j) and (j, i)), 1 for i == j
 };
 
-// Load pair pr = i * nnode + j; false when its strength is zero.
+// Unordered node pairs.  Swapping i and j keeps the centre (v_i + v_j)/2, the radius
+// |v_i - v_j|/2 and the strength a_i a_j B(|v_i - v_j|) w_m, so (i, j) and (j, i) add the same
+// M points with the same weights: each unordered pair is spread once with twice the strength.
+// Numbering: pair pr = t nnode + i is (i, (i + t) mod nnode), offsets t = 0..floor(nnode/2);
+// t = 0 is the diagonal (multiplicity 1) and, for even nnode, the row t = nnode/2 stops at
+// i = nnode/2 - 1 (its other half repeats the same pairs): unordered_pairs(nnode) in all.
+
+// Load pair pr; false when its strength is zero.
 template <typename T, int D>
 __device__ __forceinline__ bool load_pair(const SpreadArgs &p, long long pr, PairData<T, D> &P)
 {
     const int nnode = p.nnode, N = p.N;
-    const int i = (int)(pr / nnode);
-    const int j = (int)(pr - (long long)i * nnode);
+    const int t = (int)(pr / nnode);
+    const int i = (int)(pr - (long long)t * nnode);
+    int j = i + t;
+    if (j >= nnode) j -= nnode;
+    P.mult = t ? T(2) : T(1);
     const T *vnode = static_cast<const T *>(p.vnode);
     const T *acoef = static_cast<const T *>(p.a);
     const T aij = acoef[i] * acoef[j];
@@ -304,85 +315,105 @@ struct DoubleTile {  // FP64 path: FP64 partial sums
     __device__ __forceinline__ void add_small(int c, double x) const { add(c, x); }
 };
 
-// The M points of one pair.  SMALL: every contribution of the pair is known to lie in
-// (-2^31, 2^31) tile units, so the tile's cheaper add_small applies.
-template <typename T, int D, int W, typename Tile, bool SMALL>
-__device__ __forceinline__ void spread_points(const SpreadArgs &p, const PairData<T, D> &P, T sc, const Tile &tile,
-                                              int row_lo, int nrows, int plane)
+// Point m of pair P: grid coordinates x (one grid cell = 1, x = z n / (2 pi)) and strength q in
+// tile units (qbase = a_i a_j B x multiplicity x tile scale).
+template <typename T, int D>
+__device__ __forceinline__ void make_point(const SpreadArgs &p, const PairData<T, D> &P, T qbase, int m, T *x, T &q)
 {
     const T *sig = static_cast<const T *>(p.sig);
     const T *wsig = static_cast<const T *>(p.wsig);
     const T S = T(p.S), SS = S * S, invS = T(1) / S;
     const T gs = T(p.grid_scale);
-    const int nf = p.nf;
     const bool alg = (p.r == 1);
-    const T qbase = P.base * sc;
-    for (int m = 0; m < p.M; ++m) {
-        T q = qbase * wsig[m];
-        T x[D];
+    q = qbase * wsig[m];
 #pragma unroll
-        for (int l = 0; l < D; ++l) {
-            const T vp = P.cen[l] + P.rad * sig[m * D + l];
-            T z, m2;
-            if constexpr (sizeof(T) == 4) {
-                angle_weight_f32(vp, S, invS, alg, z, m2);
-            } else if (alg) {
-                z = Fn<T>::atan2_(S, vp);
-                m2 = (SS + vp * vp) * invS;
-            } else {
-                const T u = vp * invS;
-                z = Fn<T>::atan2_(T(1), Fn<T>::sinh_(u));
-                m2 = S * Fn<T>::cosh_(u);
-            }
-            q *= m2;
-            x[l] = z * gs;
+    for (int l = 0; l < D; ++l) {
+        const T vp = P.cen[l] + P.rad * sig[m * D + l];
+        T z, m2;
+        if constexpr (sizeof(T) == 4) {
+            angle_weight_f32(vp, S, invS, alg, z, m2);
+        } else if (alg) {
+            z = Fn<T>::atan2_(S, vp);
+            m2 = (SS + vp * vp) * invS;
+        } else {
+            const T u = vp * invS;
+            z = Fn<T>::atan2_(T(1), Fn<T>::sinh_(u));
+            m2 = S * Fn<T>::cosh_(u);
         }
-        T w0[W];
-        int r0[W];
-        axis_weights<T, W>(p, x[0], w0, r0);
-        bool hit = false;
+        q *= m2;
+        x[l] = z * gs;
+    }
+}
+
+// Add the w^d contributions of one point to the rows row_lo..row_lo+nrows-1 of the block tile.
+// SMALL: every contribution is known to lie in (-2^31, 2^31) tile units, so the tile's cheaper
+// add_small applies.  SLAB: the tile holds a slab of the grid's rows and rows outside it are
+// skipped; otherwise it holds every row (row_lo = 0, nrows = n/2 + 1).
+template <typename T, int D, int W, typename Tile, bool SMALL, bool SLAB>
+__device__ __forceinline__ void spread_point(const SpreadArgs &p, const T *x, T q, const Tile &tile, int row_lo,
+                                             int nrows, int plane)
+{
+    const int nf = p.nf;
+    T w0[W];
+    int r0[W];
+    axis_weights<T, W>(p, x[0], w0, r0);
+    bool hit = !SLAB;
 #pragma unroll
-        for (int a = 0; a < W; ++a) {
+    for (int a = 0; a < W; ++a) {
+        if constexpr (SLAB) {
             r0[a] -= row_lo;
             hit |= ((unsigned)r0[a] < (unsigned)nrows);
-            w0[a] *= q;
         }
-        if (!hit) continue;
-        T w1[W];
-        int c1[W];
-        axis_weights<T, W>(p, x[1], w1, c1);
-        if (D == 2) {
+        w0[a] *= q;
+    }
+    if (!hit) return;
+    T w1[W];
+    int c1[W];
+    axis_weights<T, W>(p, x[1], w1, c1);
+    if (D == 2) {
 #pragma unroll
-            for (int a = 0; a < W; ++a) {
-                if ((unsigned)r0[a] >= (unsigned)nrows) continue;
-                const int row = r0[a] * plane;
+        for (int a = 0; a < W; ++a) {
+            if (SLAB && (unsigned)r0[a] >= (unsigned)nrows) continue;
+            const int row = r0[a] * plane;
 #pragma unroll
-                for (int b = 0; b < W; ++b) {
-                    if constexpr (SMALL) tile.add_small(row + c1[b], w0[a] * w1[b]);
-                    else tile.add(row + c1[b], w0[a] * w1[b]);
-                }
-            }
-        } else {
-            T w2[W];
-            int c2[W];
-            axis_weights<T, W>(p, x[D - 1], w2, c2);
-#pragma unroll
-            for (int b = 0; b < W; ++b) c1[b] *= nf;
-            for (int a = 0; a < W; ++a) {
-                if ((unsigned)r0[a] >= (unsigned)nrows) continue;
-                const int row = r0[a] * plane;
-#pragma unroll
-                for (int b = 0; b < W; ++b) {
-                    const T wab = w0[a] * w1[b];
-                    const int line = row + c1[b];
-#pragma unroll
-                    for (int c = 0; c < W; ++c) {
-                        if constexpr (SMALL) tile.add_small(line + c2[c], wab * w2[c]);
-                        else tile.add(line + c2[c], wab * w2[c]);
-                    }
-                }
+            for (int b = 0; b < W; ++b) {
+                if constexpr (SMALL) tile.add_small(row + c1[b], w0[a] * w1[b]);
+                else tile.add(row + c1[b], w0[a] * w1[b]);
             }
         }
+    } else {
+        T w2[W];
+        int c2[W];
+        axis_weights<T, W>(p, x[D - 1], w2, c2);
+#pragma unroll
+        for (int b = 0; b < W; ++b) c1[b] *= nf;
+        for (int a = 0; a < W; ++a) {
+            if (SLAB && (unsigned)r0[a] >= (unsigned)nrows) continue;
+            const int row = r0[a] * plane;
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                const T wab = w0[a] * w1[b];
+                const int line = row + c1[b];
+#pragma unroll
+                for (int c = 0; c < W; ++c) {
+                    if constexpr (SMALL) tile.add_small(line + c2[c], wab * w2[c]);
+                    else tile.add(line + c2[c], wab * w2[c]);
+                }
+            }
+        }
+    }
+}
+
+// The M points of one pair, into a tile that holds every row of the grid.
+template <typename T, int D, int W, typename Tile, bool SMALL>
+__device__ __forceinline__ void spread_points(const SpreadArgs &p, const PairData<T, D> &P, T sc, const Tile &tile,
+                                              int row_lo, int nrows, int plane)
+{
+    const T qbase = P.base * sc;
+    for (int m = 0; m < p.M; ++m) {
+        T x[D], q;
+        make_point<T, D>(p, P, qbase, m, x, q);
+        spread_point<T, D, W, Tile, SMALL, false>(p, x, q, tile, row_lo, nrows, plane);
     }
 }
 
@@ -400,6 +431,99 @@ __device__ __forceinline__ void spread_pair(const SpreadArgs &p, const PairData<
         }
     }
     spread_points<T, D, W, Tile, false>(p, P, sc, tile, row_lo, nrows, plane);
+}
+
+// ---- slabbed grids: warp point queues
+//
+// When the folded grid is split into slabs along axis 0, a point adds to a block's slab only
+// if one of its w axis-0 rows lies there, and with a few slabs most points of a warp miss it:
+// spreading them where they are generated would leave most lanes idle while the others add.
+// Instead each warp appends the points that hit its slab to a queue of 32 entries in shared
+// memory (D coordinates and the strength, slot-major) and spreads a full queue with all 32
+// lanes, one point per lane.
+
+// Whether any of the w axis-0 rows of a point at grid coordinate x0 lies in the slab (the
+// rows of axis_weights).
+template <typename T, int W>
+__device__ __forceinline__ bool rows_hit(const SpreadArgs &p, T x0, int row_lo, int nrows)
+{
+    const int s = (int)Fn<T>::floor_(x0 - T(0.5 * W)) + 1;
+    const bool simple = p.simple_fold != 0;
+    bool hit = false;
+#pragma unroll
+    for (int a = 0; a < W; ++a) hit |= (unsigned)(fold_cell(s + a, p.n, simple) - row_lo) < (unsigned)nrows;
+    return hit;
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void queue_put(T *buf, int slot, const T *x, T q)
+{
+#pragma unroll
+    for (int l = 0; l < D; ++l) buf[l * 32 + slot] = x[l];
+    buf[D * 32 + slot] = q;
+}
+
+// Spread queue slot `lane` (when valid) with the whole warp; the FP32 fast add applies when
+// every queued strength is below 2^30 tile units (kernel weights are <= 1).
+template <typename T, int D, int W, typename Tile>
+__device__ __forceinline__ void queue_spread(const SpreadArgs &p, const T *buf, int lane, bool valid,
+                                             const Tile &tile, int row_lo, int nrows, int plane)
+{
+    T x[D], q = T(0);
+    if (valid) {
+#pragma unroll
+        for (int l = 0; l < D; ++l) x[l] = buf[l * 32 + lane];
+        q = buf[D * 32 + lane];
+    }
+    if constexpr (sizeof(T) == 4) {
+        const bool small = __all_sync(0xffffffffu, fabsf(q) < 1073741824.0f);
+        if (!valid) return;
+        if (small) spread_point<T, D, W, Tile, true, true>(p, x, q, tile, row_lo, nrows, plane);
+        else spread_point<T, D, W, Tile, false, true>(p, x, q, tile, row_lo, nrows, plane);
+    } else {
+        if (valid) spread_point<T, D, W, Tile, false, true>(p, x, q, tile, row_lo, nrows, plane);
+    }
+}
+
+// The pairs pr = first, first + nthr, ... of one thread, spread into one slab through the
+// warp's queue `buf` ((D + 1) x 32 values).  Every loop condition is uniform over the warp.
+template <typename T, int D, int W, typename Tile>
+__device__ __forceinline__ void spread_pairs_queued(const SpreadArgs &p, long long first, long long nthr, T sc, T tau,
+                                                    const Tile &tile, int row_lo, int nrows, int plane, T *buf)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    int count = 0;  // queued points, the same in every lane
+    for (long long pr = first; __any_sync(full, pr < p.npairs); pr += nthr) {
+        PairData<T, D> P;
+        bool ok = pr < p.npairs && load_pair<T, D>(p, pr, P);
+        if (ok && tau > T(0) && pair_bound<T, D>(p, P) < tau) ok = false;
+        if (!__any_sync(full, ok)) continue;
+        const T qbase = ok ? P.base * P.mult * sc : T(0);
+        for (int m = 0; m < p.M; ++m) {
+            T x[D], q = T(0);
+            bool hit = false;
+            if (ok) {
+                make_point<T, D>(p, P, qbase, m, x, q);
+                hit = rows_hit<T, W>(p, x[0], row_lo, nrows);
+            }
+            const unsigned mask = __ballot_sync(full, hit);
+            const int n = __popc(mask), rank = __popc(mask & lt), room = 32 - count;
+            if (hit && rank < room) queue_put<T, D>(buf, count + rank, x, q);
+            if (n >= room) {  // full: spread 32 points, then queue the rest
+                __syncwarp();
+                queue_spread<T, D, W, Tile>(p, buf, lane, true, tile, row_lo, nrows, plane);
+                __syncwarp();
+                if (hit && rank >= room) queue_put<T, D>(buf, rank - room, x, q);
+                count = n - room;
+            } else {
+                count += n;
+            }
+        }
+    }
+    __syncwarp();
+    queue_spread<T, D, W, Tile>(p, buf, lane, lane < count, tile, row_lo, nrows, plane);
 }
 
 struct SlabGeom {
@@ -453,11 +577,18 @@ __global__ void __launch_bounds__(kMaxThreadsF32) k_spread_f32(const __grid_cons
     const float tau = (float)*p.tau;
     long long first, nthr;
     pair_schedule(p, first, nthr);
-    for (long long pr = first; pr < p.npairs; pr += nthr) {
-        PairData<float, D> P;
-        if (!load_pair<float, D>(p, pr, P)) continue;
-        if (tau > 0.0f && pair_bound<float, D>(p, P) < tau) continue;
-        spread_pair<float, D, W>(p, P, sc, tile, G.row_lo, G.nrows, G.plane);
+    if (p.nslab > 1) {
+        float *buf = reinterpret_cast<float *>(smem_raw + (size_t)p.rows_per_slab * G.plane * 8) +
+                     (threadIdx.x >> 5) * 32 * (D + 1);
+        spread_pairs_queued<float, D, W>(p, first, nthr, sc, tau, tile, G.row_lo, G.nrows, G.plane, buf);
+    } else {
+        for (long long pr = first; pr < p.npairs; pr += nthr) {
+            PairData<float, D> P;
+            if (!load_pair<float, D>(p, pr, P)) continue;
+            if (tau > 0.0f && pair_bound<float, D>(p, P) < tau) continue;
+            P.base *= P.mult;
+            spread_pair<float, D, W>(p, P, sc, tile, G.row_lo, G.nrows, G.plane);
+        }
     }
     __syncthreads();
     unsigned long long *gdst = p.grid + (size_t)G.row_lo * G.plane;
@@ -482,11 +613,18 @@ __global__ void __launch_bounds__(kMaxThreadsF64) k_spread_f64(const __grid_cons
     const double tau = *p.tau;
     long long first, nthr;
     pair_schedule(p, first, nthr);
-    for (long long pr = first; pr < p.npairs; pr += nthr) {
-        PairData<double, D> P;
-        if (!load_pair<double, D>(p, pr, P)) continue;
-        if (tau > 0.0 && pair_bound<double, D>(p, P) < tau) continue;
-        spread_pair<double, D, W>(p, P, 1.0, tile, G.row_lo, G.nrows, G.plane);
+    if (p.nslab > 1) {
+        double *buf = reinterpret_cast<double *>(smem_raw + (size_t)p.rows_per_slab * G.plane * 8) +
+                      (threadIdx.x >> 5) * 32 * (D + 1);
+        spread_pairs_queued<double, D, W>(p, first, nthr, 1.0, tau, tile, G.row_lo, G.nrows, G.plane, buf);
+    } else {
+        for (long long pr = first; pr < p.npairs; pr += nthr) {
+            PairData<double, D> P;
+            if (!load_pair<double, D>(p, pr, P)) continue;
+            if (tau > 0.0 && pair_bound<double, D>(p, P) < tau) continue;
+            P.base *= P.mult;
+            spread_pair<double, D, W>(p, P, 1.0, tile, G.row_lo, G.nrows, G.plane);
+        }
     }
     __syncthreads();
     // block partial sums -> the grid's fixed-point unit (|v| 2^Eg <= 2^61); the rounding of a

@@ -106,7 +106,8 @@ def test_full_size_2d_hard_spheres_fp32_sampled_modes():
     modes = sample_modes(d, N, 48, seed=11)
     gain, loss = O.collide_parts(ft, d, N, M, S, gamma, r=1, modes=modes)
     Q, info, mom = gpu_collide(ft, d, N, M, S, gamma, 1e-6, precision=PG_PREC_FP32)  # bench.py's plan
-    assert info["points"] == M * N ** (2 * d)
+    nn = N ** d
+    assert info["pairs"] == nn * (nn + 1) // 2 and info["points"] == M * info["pairs"]  # unordered pairs
     assert rel_l2(Q[flat_index(modes, N)], gain - loss) < TOL32
     ma, en = O.mass_energy_coeffs(d, N, S)
     assert abs(mom["mass"]) <= 1e-6 * abs(mom["mass_gain"])

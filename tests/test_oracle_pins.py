@@ -199,22 +199,28 @@ def _qbkw2(p, t):
             + 1 / (2 * math.pi * K * K) * np.exp(-v2 / (2 * K)) * (2 - v2 / (2 * K * K))) * Kp
 
 
-def test_bkw2d_matches_paper_table():
-    """Best-S L2 error of Q_N against Q_BKW at t = 2 on the paper's 200^2 grid agrees with the
-    paper's Chebyshev-0 column within a factor 4 (their S scan and norm are not restated)."""
-    rows = [l.split() for l in open(os.path.join(GOLDEN, "bkw2d_chebyshev0_l2.txt")) if l[0] != "#"]
+@pytest.mark.parametrize("r,scans", [
+    (0, ((8, (2.0, 2.25, 2.5)), (16, (2.25, 2.5, 2.75, 3.0)))),
+    (1, ((8, (2.0, 2.25, 2.5)), (16, (2.5, 2.75, 3.0)))),
+])
+def test_bkw2d_matches_paper_table(r, scans):
+    """Best-S L2 error of Q_N against Q_BKW at t = 2 on the paper's 200^2 grid (Section 5.1.1,
+    Test 01) agrees with the paper's Chebyshev-0 (r = 0) and Chebyshev-1 (r = 1) columns within a
+    factor 4 (their S scan and norm are not restated)."""
+    name = "bkw2d_chebyshev0_l2.txt" if r == 0 else "bkw2d_chebyshev1_l2.txt"
+    rows = [l.split() for l in open(os.path.join(GOLDEN, name)) if l[0] != "#"]
     paper = {int(a): float(b) for a, b in rows}
     x = np.linspace(-6.3, 6.3, 200)
     X, Y = np.meshgrid(x, x, indexing="ij")
     pts = np.stack([X.ravel(), Y.ravel()], 1)
     h = x[1] - x[0]
     exact = _qbkw2(pts, 2.0)
-    for N, Ss in ((8, (2.0, 2.25, 2.5)), (16, (2.25, 2.5, 2.75, 3.0))):
+    for N, Ss in scans:
         best = np.inf
         for S in Ss:
-            ft = O.project(lambda p: W.bkw_2d(p, t=2.0), 2, N, S, 0)
-            Q = O.collide(ft, 2, N, N, S, 0.0, r=0)
-            QN = O.fN_values(Q, 2, N, S, 0, pts)
+            ft = O.project(lambda p: W.bkw_2d(p, t=2.0), 2, N, S, r)
+            Q = O.collide(ft, 2, N, N, S, 0.0, r=r)
+            QN = O.fN_values(Q, 2, N, S, r, pts)
             best = min(best, math.sqrt(np.sum((QN - exact) ** 2) * h * h))
         assert paper[N] / 4 < best < paper[N] * 4, (N, best, paper[N])
 
