@@ -30,6 +30,10 @@ if ROOT not in sys.path:
 
 METRIC = "Q(f,f) evals/s and NU points/s at stated rel err; FP32/batched vs FP64, % roofline"
 UNIT = "Q evals/s"
+# DRAM bytes (read + write) of one launch of the spreading kernel on this workload, from the ncu
+# capture summarised in profiles/k_spread_f32_2d_w6_N64_full.md; keyed by kernel and
+# configuration, to be re-taken whenever the kernel changes.
+PROFILED_TRAFFIC = {("k_spread_f32<2,6>", 64, 32, 1e-6): 220416}
 
 
 def parse():
@@ -312,7 +316,7 @@ def run_ours(args):
     mom = plan64.moments()
 
     # roofline of the dominant kernel (spreading): one shared-memory atomic add per
-    # contribution, M N^(2d) w^d contributions per launch
+    # contribution, w^d contributions for each of the M N^d (N^d + 1)/2 points per launch
     spread_ms = statistics.mean(s[2] for s in st32)
     wgt = info32["kernel_width"]
     rmw_per_launch = info32["points"] * wgt ** d
@@ -363,7 +367,8 @@ def run_ours(args):
         "conservation_fp64": {"mass_rel": abs(mom["mass"]) / abs(mom["mass_gain"]),
                               "energy_rel": abs(mom["energy"]) / abs(mom["energy_gain"])},
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_rmw / 1e9,
-                     "unit": "G shared-memory RMW/s", "frac": achieved / peak_rmw, "traffic": None,
+                     "unit": "G shared-memory RMW/s", "frac": achieved / peak_rmw,
+                     "traffic": PROFILED_TRAFFIC.get((f"k_spread_f32<{d},{wgt}>", N, M, args.tol32)),
                      "kernel": "k_spread<float,2,%d>" % wgt,
                      "peak_basis": f"{sm_count} SMs x 32 shared-memory lanes/clk x 2070 MHz (derived)",
                      "measured_atomic_peak": measured_atomic / 1e9,

@@ -200,6 +200,16 @@ int pg_boltz_project(pg_boltz_plan_t *plan, const double *fvals_dev, double *fti
 int pg_boltz_evaluate(pg_boltz_plan_t *plan, const double *coef_dev, long long npts, const double *pts_dev,
                       double *out_dev);
 
+/*
+ * Adaptive map scale (Section 5, the choice of S stated before the 2D examples): the S for
+ * which the first interior node xi_2 = -cos(pi/(N+1)) of the M_v = N + 2 Chebyshev-Gauss-Lobatto
+ * nodes maps to v = -L (and, by symmetry, the last interior node to +L):
+ *   algebraic map (map_log = 0):   S = L tan(pi/(N+1))
+ *   logarithmic map (map_log = 1): S = L / atanh(cos(pi/(N+1)))
+ * Host-only.  *S_out receives S.  PG_ERR_ARG for N < 2, L not finite or <= 0, S_out NULL.
+ */
+int pg_boltz_adaptive_scale(int N, double L, int map_log, double *S_out);
+
 /* Describe the plan (host-only). */
 int pg_boltz_info(const pg_boltz_plan_t *plan, pg_boltz_info_t *out);
 

@@ -26,6 +26,7 @@ EXPORTS = (
     "pg_boltz_stage_times", "pg_boltz_project_noalloc", "pg_boltz_probe_shared_atomics",
     "pg_boltz_plan_batched", "pg_boltz_plan_batched_ex", "pg_boltz_collide_batched", "pg_boltz_batched_offsets",
     "pg_boltz_batched_use_graph", "pg_boltz_rk4", "pg_boltz_conservation", "pg_boltz_evaluate",
+    "pg_boltz_adaptive_scale",
 )
 
 
@@ -82,6 +83,7 @@ def lib():
     L.pg_boltz_project_nodes.argtypes = [vp, dp, ip]
     L.pg_boltz_project.argtypes = [vp, vp, vp]
     L.pg_boltz_evaluate.argtypes = [vp, vp, ctypes.c_longlong, vp, vp]
+    L.pg_boltz_adaptive_scale.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, dp]
     L.pg_boltz_info.argtypes = [vp, ctypes.POINTER(Info)]
     L.pg_boltz_destroy.argtypes = [vp]
     L.pg_boltz_destroy.restype = None
@@ -136,6 +138,13 @@ def probe_shared_atomics(stream=None) -> float:
     out = ctypes.c_double(0.0)
     raw = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     _check(lib().pg_boltz_probe_shared_atomics(ctypes.c_void_p(raw), ctypes.byref(out)))
+    return out.value
+
+
+def adaptive_scale(N: int, L: float, map_log: bool = False) -> float:
+    """S with v(xi_2) = -L for the M_v = N + 2 node grid (host-only, pg_boltz_adaptive_scale)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().pg_boltz_adaptive_scale(int(N), float(L), int(bool(map_log)), ctypes.byref(out)))
     return out.value
 
 

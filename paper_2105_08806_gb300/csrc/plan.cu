@@ -569,6 +569,18 @@ PG_API int pg_boltz_project(pg_boltz_plan_t *p, const double *fvals_dev, double 
     return PG_OK;
 }
 
+// v(xi_2) = -L with xi_2 = -cos(pi/(N+1)): for r = 1, v = S xi / sqrt(1 - xi^2) gives
+// S = L sin(phi) / cos(phi) with phi = pi/(N+1); for r = 0, v = S atanh(xi) gives S = L / atanh(cos phi).
+PG_API int pg_boltz_adaptive_scale(int N, double L, int map_log, double *S_out)
+{
+    if (!S_out) return set_error(PG_ERR_ARG, "S_out is NULL");
+    if (N < 2) return set_error(PG_ERR_ARG, "need N >= 2");
+    if (!std::isfinite(L) || L <= 0.0) return set_error(PG_ERR_ARG, "L must be finite and > 0");
+    const double phi = kPi / (N + 1);
+    *S_out = map_log ? L / std::atanh(std::cos(phi)) : L * std::tan(phi);
+    return PG_OK;
+}
+
 PG_API int pg_boltz_info(const pg_boltz_plan_t *p, pg_boltz_info_t *out)
 {
     if (!p || !out) return set_error(PG_ERR_ARG, "NULL argument");

@@ -71,3 +71,23 @@ def test_extended_option_validation(L):
     o = _lib.Opts(d=2, N=8, M=8, S=2.0, kernel_gamma=0.0, tol=1e-6, map_log=3)
     assert not L.pg_boltz_plan_ex(ctypes.byref(o))
     assert "map_log" in _lib.last_error()
+
+
+@pytest.mark.parametrize("r", [0, 1])
+@pytest.mark.parametrize("N,Lt", [(2, 5.0), (8, 8.83), (32, 14.35), (64, 13.24)])
+def test_adaptive_scale_maps_first_interior_node_to_minus_L(L, r, N, Lt):
+    """Section 5: S is chosen so that xi_2 and xi_{N+1} of the M_v = N + 2 CGL nodes map to -L and
+    L; checked with the oracle's own map (an independent implementation of Eq. 1D_mapping)."""
+    from oracle import oracle as O
+    S = _lib.adaptive_scale(N, Lt, map_log=(r == 0))
+    xi = O.cgl(N + 2)[0]
+    v = O.v_of_xi(xi[1:-1], S, r)
+    assert abs(v[0] + Lt) <= 1e-12 * Lt and abs(v[-1] - Lt) <= 1e-12 * Lt
+
+
+def test_adaptive_scale_rejects_bad_arguments(L):
+    out = ctypes.c_double(0.0)
+    assert L.pg_boltz_adaptive_scale(1, 5.0, 0, ctypes.byref(out)) == _lib.PG_ERR_ARG
+    assert L.pg_boltz_adaptive_scale(8, 0.0, 0, ctypes.byref(out)) == _lib.PG_ERR_ARG
+    assert L.pg_boltz_adaptive_scale(8, float("inf"), 1, ctypes.byref(out)) == _lib.PG_ERR_ARG
+    assert L.pg_boltz_adaptive_scale(8, 5.0, 0, None) == _lib.PG_ERR_ARG

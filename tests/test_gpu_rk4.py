@@ -73,7 +73,8 @@ def test_two_maxwellian_moments_follow_closed_forms():
     A = np.array([float(x[4]) for x in rows])
     C = np.array([float(x[5]) for x in rows])
     N, L, dt, T = 32, 14.35, 0.02, 1.0
-    S = L / math.atanh(math.cos(math.pi / (N + 1)))
+    from paper_2105_08806_gb300 import adaptive_scale
+    S = adaptive_scale(N, L, map_log=True)  # v(xi_2) = -L (Section 5)
     f0 = lambda p: W.maxwellian(p, 0.5, [-1, 2], 1.0) + W.maxwellian(p, 0.5, [3, -3], 1.0)
     ft = O.project(f0, 2, N, S, 0).ravel()
     m0 = _moments(ft, N, S, 0)
