@@ -56,7 +56,7 @@ def _lib():
     dp = ctypes.POINTER(ctypes.c_double)
     ip = ctypes.POINTER(ctypes.c_int)
     common = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_int, dp, dp,
-              ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+              ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]
     lib.pgb_oracle_collide.argtypes = common + [ctypes.c_int, ip, ctypes.c_long, ctypes.c_long, dp, dp,
                                                 ctypes.c_int]
     lib.pgb_oracle_collide.restype = ctypes.c_int
@@ -273,7 +273,7 @@ def all_modes(d: int, N: int):
 class Problem:
     """Quadrature data of one discrete operator: nodes, weights, g_i, sphere set, kernel."""
 
-    def __init__(self, ftilde, d, N, M, S, gamma, r=1, sphere="auto"):
+    def __init__(self, ftilde, d, N, M, S, gamma, r=1, sphere="auto", angular=None):
         self.d, self.N, self.M, self.S, self.gamma, self.r = d, N, M, float(S), float(gamma), int(r)
         xi, v, w, mu2 = interior_nodes(N, S, r)
         self.v1d = np.ascontiguousarray(v)
@@ -284,20 +284,24 @@ class Problem:
         self.wsig = np.ascontiguousarray(wsig)
         # B = |v - v_*|^gamma / |S^{d-1}|  (VHS kernel, Section 3.1; constant 1/|S^{d-1}| as in Section 5 BKW tests)
         self.Bconst = 1.0 / sphere_area(d)
+        # angular factor b(cos theta) = sum_p angular[p] cos^p theta of B(|g|, cos theta)
+        # (Eq. collision_form); None: b = 1
+        self.bcoef = np.ascontiguousarray(np.asarray(angular if angular is not None else [], dtype=np.float64))
 
     def _common(self):
         return (self.d, self.N, _dp(self.v1d), _dp(self.g), self.Wnode, self.M, _dp(self.sig),
-                _dp(self.wsig), self.S, self.r, self.gamma, self.Bconst)
+                _dp(self.wsig), self.S, self.r, self.gamma, self.Bconst, int(self.bcoef.size),
+                _dp(self.bcoef) if self.bcoef.size else None)
 
 
 def collide_parts(ftilde, d, N, M, S, gamma, r=1, sphere="auto", modes=None, nthreads=None,
-                  outer=None):
+                  outer=None, angular=None):
     """(gain, loss) for the requested modes (default: all (N+1)^d, C-order).
 
     `outer` = (i_lo, i_hi) restricts the outer node sum to i_lo <= i < i_hi (C-order node
     index); the default is every node.
     """
-    pb = Problem(ftilde, d, N, M, S, gamma, r, sphere)
+    pb = Problem(ftilde, d, N, M, S, gamma, r, sphere, angular)
     modes = all_modes(d, N) if modes is None else np.ascontiguousarray(np.asarray(modes, dtype=np.int32))
     nm = modes.shape[0]
     gain = np.zeros(nm)
@@ -310,18 +314,18 @@ def collide_parts(ftilde, d, N, M, S, gamma, r=1, sphere="auto", modes=None, nth
     return gain, loss
 
 
-def collide(ftilde, d, N, M, S, gamma, r=1, sphere="auto", modes=None, nthreads=None):
+def collide(ftilde, d, N, M, S, gamma, r=1, sphere="auto", modes=None, nthreads=None, angular=None):
     """Q_k = gain - loss (Section 4.2, Q = Q+ - Q-)."""
-    gain, loss = collide_parts(ftilde, d, N, M, S, gamma, r, sphere, modes, nthreads)
+    gain, loss = collide_parts(ftilde, d, N, M, S, gamma, r, sphere, modes, nthreads, angular=angular)
     return gain - loss
 
 
 PHI_ONE, PHI_V, PHI_V2, PHI_VV, PHI_VV2 = 0, 1, 2, 3, 4
 
 
-def weak(ftilde, d, N, M, S, gamma, phis, r=1, sphere="auto", nthreads=None):
+def weak(ftilde, d, N, M, S, gamma, phis, r=1, sphere="auto", nthreads=None, angular=None):
     """sum qbar [phi(v') - phi(v_i)] and its scale for each (kind, a, b) in phis (Eq. weak)."""
-    pb = Problem(ftilde, d, N, M, S, gamma, r, sphere)
+    pb = Problem(ftilde, d, N, M, S, gamma, r, sphere, angular)
     ph = np.ascontiguousarray(np.asarray(phis, dtype=np.int32).reshape(-1, 3))
     out = np.zeros(2 * ph.shape[0])
     rc = _lib().pgb_oracle_weak(*pb._common(), ph.shape[0], _ip(ph), _dp(out),

@@ -9,7 +9,8 @@
  * What it computes (Section 3, Eq. Qk_component, with the quadrature of Section 4.1):
  *
  *   Q_k = sum_{i,j interior nodes} sum_m  qbar_{ijm} [ That_k(v'_{ijm}) - That_k(v_i) ]
- *   qbar_{ijm} = W_i W_j w_m B(|v_i - v_j|) g_i g_j
+ *   qbar_{ijm} = W_i W_j w_m B(|v_i - v_j|, cos theta_{ijm}) g_i g_j,
+ *   cos theta_{ijm} = <(v_i - v_j)/|v_i - v_j|, sigma_m>                 (Eq. collision_form)
  *   v'_{ijm}   = (v_i + v_j)/2 + |v_i - v_j| sigma_m / 2                  (Section 1)
  *   That_k(v)  = prod_l mu(xi(v_l))^{-2} T_{k_l}(xi(v_l)) / sqrt(c_{k_l})  (Section 2.1, Eq. 1DCheby)
  *
@@ -41,6 +42,8 @@ typedef struct {
     const double *sig;   /* M x d sphere points                                        */
     const double *wsig;  /* M sphere weights                                           */
     double S, gamma, Bconst;
+    int nb;              /* angular polynomial terms (0: b = 1)                        */
+    const double *bcoef; /* b(cos theta) = sum_p bcoef[p] cos^p theta                  */
     const int *modes;    /* nmodes x d mode multi-indices                              */
     /* weak functionals */
     int nphi;
@@ -92,6 +95,24 @@ static double kernel_B(double grel, double gamma, double Bconst)
     return Bconst * pow(grel, gamma);
 }
 
+/* Angular factor b(cos theta) of B(|g|, cos theta) = Bconst |g|^gamma b(cos theta) (Eq. collision_form),
+ * cos theta = <(v - v_*)/|v - v_*|, sigma>; taken as 0 when v = v_*.  nb = 0: b = 1 (VHS). */
+static double angular_b(const prob_t *p, const double *vi, const double *vj, double grel, const double *sig)
+{
+    if (p->nb == 0) return 1.0;
+    double c = 0.0;
+    if (grel > 0.0) {
+        for (int l = 0; l < p->d; ++l) c += (vi[l] - vj[l]) * sig[l];
+        c /= grel;
+    }
+    double b = 0.0, cp = 1.0;
+    for (int t = 0; t < p->nb; ++t) {
+        b += p->bcoef[t] * cp;
+        cp *= c;
+    }
+    return b;
+}
+
 /* Weak-form test functions used for conservation and moment checks:
  * kind 0: 1;  kind 1: v_a;  kind 2: |v|^2;  kind 3: v_a v_b;  kind 4: v_a |v|^2. */
 static double phi_eval(const int *ph, const double *v, int d)
@@ -136,7 +157,7 @@ static void *worker(void *arg)
             double B = kernel_B(grel, p->gamma, p->Bconst);
             double pair = p->Wnode * p->Wnode * B * p->g[i] * p->g[j];
             for (int m = 0; m < p->M; ++m) {
-                double qbar = pair * p->wsig[m];
+                double qbar = pair * p->wsig[m] * angular_b(p, vi, vj, grel, p->sig + m * d);
                 inner += qbar;
                 for (int l = 0; l < d; ++l)
                     vp[l] = 0.5 * (vi[l] + vj[l]) + 0.5 * grel * p->sig[m * d + l];
@@ -207,16 +228,18 @@ static int run(prob_t *p, long i_lo, long i_hi, int nthreads, double *gain, doub
  */
 int pgb_oracle_collide(int d, int Nn, const double *v1d, const double *g, double Wnode,
                        int M, const double *sig, const double *wsig,
-                       double S, int r, double gamma, double Bconst,
+                       double S, int r, double gamma, double Bconst, int nb, const double *bcoef,
                        int nmodes, const int *modes, long i_lo, long i_hi,
                        double *gain, double *loss, int nthreads)
 {
-    if (d < 1 || d > ORACLE_MAX_D || Nn < 1 || M < 1 || nmodes < 1 || (r != 0 && r != 1)) return -1;
+    if (d < 1 || d > ORACLE_MAX_D || Nn < 1 || M < 1 || nmodes < 1 || (r != 0 && r != 1) || nb < 0 ||
+        (nb > 0 && !bcoef))
+        return -1;
     prob_t p;
     memset(&p, 0, sizeof(p));
     p.d = d; p.Nn = Nn; p.M = M; p.r = r; p.nmodes = nmodes;
     p.v1d = v1d; p.g = g; p.Wnode = Wnode; p.sig = sig; p.wsig = wsig;
-    p.S = S; p.gamma = gamma; p.Bconst = Bconst; p.modes = modes;
+    p.S = S; p.gamma = gamma; p.Bconst = Bconst; p.nb = nb; p.bcoef = bcoef; p.modes = modes;
     p.kmax = 0;
     for (int t = 0; t < nmodes * d; ++t) if (modes[t] > p.kmax) p.kmax = modes[t];
     long nnode = 1;
@@ -252,15 +275,15 @@ int pgb_oracle_collide(int d, int Nn, const double *v1d, const double *g, double
  */
 int pgb_oracle_weak(int d, int Nn, const double *v1d, const double *g, double Wnode,
                     int M, const double *sig, const double *wsig,
-                    double S, int r, double gamma, double Bconst,
+                    double S, int r, double gamma, double Bconst, int nb, const double *bcoef,
                     int nphi, const int *phi, double *out, int nthreads)
 {
-    if (d < 1 || d > ORACLE_MAX_D || Nn < 1 || M < 1 || nphi < 1) return -1;
+    if (d < 1 || d > ORACLE_MAX_D || Nn < 1 || M < 1 || nphi < 1 || nb < 0 || (nb > 0 && !bcoef)) return -1;
     prob_t p;
     memset(&p, 0, sizeof(p));
     p.d = d; p.Nn = Nn; p.M = M; p.r = r; p.nmodes = 0;
     p.v1d = v1d; p.g = g; p.Wnode = Wnode; p.sig = sig; p.wsig = wsig;
-    p.S = S; p.gamma = gamma; p.Bconst = Bconst; p.nphi = nphi; p.phi = phi;
+    p.S = S; p.gamma = gamma; p.Bconst = Bconst; p.nb = nb; p.bcoef = bcoef; p.nphi = nphi; p.phi = phi;
     long nnode = 1;
     for (int l = 0; l < d; ++l) nnode *= Nn;
     double *lossw = (double *)calloc((size_t)nnode, sizeof(double));

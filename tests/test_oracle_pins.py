@@ -261,3 +261,67 @@ def test_moments_2d_closed_form():
     ft = O.project(f0, 2, N, S, 0)
     val, _ = O.weak(ft, 2, N, N, S, 0.0, phis, r=0)
     assert np.abs(val - deriv0).max() < 1e-3, val - deriv0
+
+
+# ---------------------------------------------------------------- angular kernels B(|g|, cos theta)
+ANG = [1.0, 0.5, 0.3, -0.2]  # b(c) = 1 + c/2 + 0.3 c^2 - 0.2 c^3, positive on [-1, 1]
+
+
+def _ang_input(d, N, S=2.0, r=1):
+    fun = W.c1_2d_maxwell() if d == 2 else (lambda p: W.maxwellian(p, 1.0, [0.2, -0.1, 0.3], 0.9))
+    return O.project(fun, d, N, S, r)
+
+
+@pytest.mark.parametrize("d,N,M,sphere", [(2, 6, 8, "auto"), (3, 4, 8, "auto"), (3, 4, 7, "fibonacci")])
+def test_odd_angular_kernel_has_no_gain(d, N, M, sphere):
+    """b(cos theta) = cos theta: the orders (i, j) and (j, i) give the same post-collision point with
+    opposite cos theta (Eq. collision_form), so the gain sum cancels exactly for any sphere set; the
+    loss vanishes when sum_m w_m sigma_m = 0 (uniform circle, antipodal set) and not otherwise."""
+    ft = _ang_input(d, N)
+    g1, l1 = O.collide_parts(ft, d, N, M, 2.0, 0.5, sphere=sphere)
+    g, l = O.collide_parts(ft, d, N, M, 2.0, 0.5, sphere=sphere, angular=[0.0, 1.0])
+    assert np.abs(g).max() <= 1e-13 * np.abs(g1).max()
+    if sphere == "auto":
+        assert np.abs(l).max() <= 1e-13 * np.abs(l1).max()
+    else:
+        assert np.abs(l).max() > 1e-3 * np.abs(l1).max()
+
+
+@pytest.mark.parametrize("d,N,M", [(2, 6, 8), (3, 4, 8)])
+def test_odd_part_drops_out_with_antipodal_sets(d, N, M):
+    """b = 1 + cos theta and b = 1 give the same Q with an antipodal (or uniform-circle) set."""
+    ft = _ang_input(d, N)
+    q1 = O.collide(ft, d, N, M, 2.0, 1.0)
+    q2 = O.collide(ft, d, N, M, 2.0, 1.0, angular=[1.0, 1.0])
+    assert np.abs(q2 - q1).max() <= 1e-12 * np.abs(q1).max()
+
+
+def test_circle_second_moment_halves_the_loss():
+    """2D uniform circle with M >= 3 points: sum_m (2 pi/M) cos^2(theta_m - phi) = pi exactly, half of
+    sum_m w_m = 2 pi, so b = cos^2 theta gives exactly half the loss of b = 1 (Eq. Qminus)."""
+    ft = _ang_input(2, 6)
+    _, l1 = O.collide_parts(ft, 2, 6, 6, 2.0, 1.0)
+    _, l2 = O.collide_parts(ft, 2, 6, 6, 2.0, 1.0, angular=[0.0, 0.0, 1.0])
+    assert np.abs(l2 - 0.5 * l1).max() <= 1e-13 * np.abs(l1).max()
+
+
+@pytest.mark.parametrize("d,N,M,gamma,r", [(2, 8, 8, 0.0, 1), (2, 6, 12, 1.0, 0), (3, 4, 8, 0.5, 1)])
+def test_weak_form_conservation_angular(d, N, M, gamma, r):
+    """Mass, momentum and energy of the discrete weak form vanish for a general B(|g|, cos theta)
+    with an antipodal set (Eq. consv holds for every kernel of the form Eq. collision_form)."""
+    ft = _ang_input(d, N, r=r)
+    phis = [(0, 0, 0)] + [(1, l, 0) for l in range(d)] + [(2, 0, 0)]
+    val, scale = O.weak(ft, d, N, M, 2.0, gamma, phis, r=r, angular=ANG)
+    assert np.all(np.abs(val) <= 1e-13 * scale), val / scale
+
+
+def test_maxwellian_equilibrium_angular_kernel():
+    """Q(M, M) = 0 for a Maxwellian with any B(|g|, cos theta); the residual decays with N."""
+    mx = lambda p: W.maxwellian(p, 1.0, [0.3, -0.2], 1.0)
+    res = []
+    for N in (8, 16, 24):
+        ft = O.project(mx, 2, N, 2.0, 0)
+        gain, loss = O.collide_parts(ft, 2, N, N, 2.0, 0.5, r=0, angular=ANG)
+        res.append(np.linalg.norm(gain - loss) / np.linalg.norm(gain))
+    assert res[0] > res[1] > res[2]
+    assert res[2] < 1e-4
