@@ -78,6 +78,14 @@ typedef struct {
     int screen;          /* 1: skip the node pairs with the smallest strength bounds, as many
                             as keep their summed bound below 0.05 tol B (B >= the sum of all
                             point strengths); 0 (default): spread every pair.               */
+    int angular_terms;   /* 0 (default): VHS kernel B = |g|^gamma / |S^{d-1}|.  1..8: the kernel
+                            B(|g|, cos theta) = |g|^gamma b(cos theta) / |S^{d-1}| of
+                            Eq. collision_form with b(c) = sum_{p < angular_terms}
+                            angular_coef[p] c^p, cos theta = (v - v_*) . sigma / |v - v_*|
+                            (0 when v = v_*).  The loss sum then runs over the sphere set per
+                            node pair (O(M N^(2d)), as Section 4.2 states for general kernels).
+                            Plain plans only.                                               */
+    const double *angular_coef; /* host array of angular_terms finite values, copied at plan time */
 } pg_boltz_opts_t;
 
 /* Read-only description of a plan (pg_boltz_info). */

@@ -37,6 +37,7 @@ class Opts(ctypes.Structure):
         ("map_log", ctypes.c_int), ("precision", ctypes.c_int), ("sphere", ctypes.c_int),
         ("upsampfac", ctypes.c_double), ("proj_nodes", ctypes.c_int),
         ("spread_threads", ctypes.c_int), ("spread_blocks_per_sm", ctypes.c_int), ("screen", ctypes.c_int),
+        ("angular_terms", ctypes.c_int), ("angular_coef", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -153,11 +154,15 @@ class Plan:
 
     def __init__(self, d, N, M, S, kernel_gamma, tol, *, map_log=False, precision=PG_PREC_AUTO,
                  sphere=PG_SPHERE_AUTO, upsampfac=0.0, proj_nodes=0, spread_threads=0,
-                 spread_blocks_per_sm=0, screen=False):
+                 spread_blocks_per_sm=0, screen=False, angular=None):
+        """angular: coefficients of b(cos theta) = sum_p angular[p] cos^p theta (at most 8), None: VHS."""
+        ang = list(angular) if angular is not None else []
+        coef = (ctypes.c_double * max(1, len(ang)))(*ang)
         o = Opts(d=d, N=N, M=M, S=S, kernel_gamma=kernel_gamma, tol=tol, map_log=int(map_log),
                  precision=precision, sphere=sphere, upsampfac=upsampfac, proj_nodes=proj_nodes,
                  spread_threads=spread_threads, spread_blocks_per_sm=spread_blocks_per_sm,
-                 screen=int(screen))
+                 screen=int(screen), angular_terms=len(ang),
+                 angular_coef=ctypes.cast(coef, ctypes.POINTER(ctypes.c_double)))
         h = lib().pg_boltz_plan_ex(ctypes.byref(o))
         if not h:
             raise PGBoltzError(PG_ERR_ARG, last_error())

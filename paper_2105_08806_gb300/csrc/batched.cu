@@ -60,6 +60,8 @@ struct BatchArgs {
     double *Bcell;
     double *Tcell;  // per-cell screening threshold (0: spread every pair)
     unsigned long long *grid;
+    int *carry;          // FP32: per-block carry counters, blocks x carry_stride
+    int carry_stride;    // cells of the largest cell tile
     double *scratch;
     const double *v64;
     const float *v32;
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_batch_prep(const __grid_consta
                 default: B = (g2 > PT(0)) ? pow(g, gam) : PT(0); break;
                 }
                 const PT aj = PT(a[j]);
-                Lp += aj * B;
+                Lp = fma(aj, B, Lp);  // as the single-plan loss kernel
                 for (int l = 0; l < d; ++l) {
                     const PT R_ = fabs(PT(0.5) * (vi[l] + vj[l])) + PT(0.5) * g;
                     mu *= (b.r == 1) ? (S * S + R_ * R_) * invS : S * cosh(R_ * invS);
@@ -292,6 +294,10 @@ __device__ __forceinline__ void cell_args(const BatchArgs &b, const CellDesc &cd
     sa.tau = nullptr;  // the batched kernel reads Tcell directly
     sa.grid = b.grid + cd.grid_off;
     sa.simple_fold = (b.w <= cd.n / 2) ? 1 : 0;
+    sa.nang_even = 0;  // batched cells use VHS kernels
+    sa.angmax = 1.0;
+    sa.cpad = tile_col_pad(b.w);
+    sa.ncol = cd.nf + 2 * sa.cpad;
 }
 
 template <typename T>
@@ -308,9 +314,22 @@ __global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __gr
     int cur = -1, ncell = 0, plane = 0, Eg = 0, shift = 0;
     T sc = T(0), tau = T(0);
     SpreadArgs sa;
-    unsigned *lo = reinterpret_cast<unsigned *>(smem_raw);
-    int *hi = nullptr;
+    int *lo = reinterpret_cast<int *>(smem_raw);
+    int *carry = F32 ? b.carry + (size_t)blockIdx.x * b.carry_stride : nullptr;
     double *dv = reinterpret_cast<double *>(smem_raw);
+    // add the current cell's tile to its grid (padding columns folded onto their cells)
+    auto flush = [&]() {
+        for (int e = threadIdx.x; e < ncell; e += blockDim.x) {
+            const int gc = tile_to_grid_cell(e, D, s_cd.nf, sa.ncol, sa.cpad, s_cd.n, 0);
+            if constexpr (F32) {
+                const long long v = SplitTile{lo, carry}.value(e);
+                if (v) atomicAdd(sa.grid + gc, (unsigned long long)(v * (1ll << shift)));
+            } else {
+                const long long v = __double2ll_rn(dv[e] * ldexp(1.0, Eg));
+                if (v) atomicAdd(sa.grid + gc, (unsigned long long)v);
+            }
+        }
+    };
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(b.counter, 1);
@@ -319,37 +338,24 @@ __global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __gr
         if (item >= b.nitems) break;  // uniform over the block
         const int cell = b.item_cell[item];
         if (cell != cur) {
-            if (cur >= 0) {
-                // add the previous cell's tile to its grid
-                unsigned long long *g = sa.grid;
-                for (int e = threadIdx.x; e < ncell; e += blockDim.x) {
-                    if constexpr (F32) {
-                        const long long v = (long long)(((unsigned long long)(unsigned)hi[e] << 32) | lo[e]);
-                        if (v && shift <= 62) atomicAdd(g + e, (unsigned long long)(v * (1ll << shift)));
-                    } else {
-                        const long long v = __double2ll_rn(dv[e] * ldexp(1.0, Eg));
-                        if (v) atomicAdd(g + e, (unsigned long long)v);
-                    }
-                }
-            }
+            if (cur >= 0) flush();  // the previous cell's tile
             __syncthreads();
             if (threadIdx.x == 0) s_cd = b.cells[cell];
             __syncthreads();
             cur = cell;
             cell_args(b, s_cd, F32, sa);
-            plane = (D == 3) ? s_cd.nf * s_cd.nf : s_cd.nf;
+            plane = (D == 3) ? s_cd.nf * sa.ncol : sa.ncol;
             ncell = plane * s_cd.nf;
-            hi = reinterpret_cast<int *>(smem_raw) + ncell;
             const double Bc = b.Bcell[cell];
             Eg = global_exponent(Bc);
-            const int Et = F32 ? min(Eg - 10, 120) : Eg;
+            const int Et = F32 ? min(Eg - kTileBits, 120) : Eg;
             shift = Eg - Et;
             sc = F32 ? T(ldexp(1.0, Et)) : T(1);
             tau = T(b.Tcell[cell]);
             for (int e = threadIdx.x; e < ncell; e += blockDim.x) {
                 if constexpr (F32) {
-                    lo[e] = 0u;
-                    hi[e] = 0;
+                    lo[e] = 0;
+                    carry[e] = 0;
                 } else {
                     dv[e] = 0.0;
                 }
@@ -365,25 +371,15 @@ __global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __gr
             if (tau > T(0) && pair_bound<T, D>(sa, P) < tau) continue;
             P.base *= P.mult;
             if constexpr (F32) {
-                spread_pair<T, D, W>(sa, P, sc, SplitTile{lo, hi}, 0, s_cd.nf, plane);
+                const SplitTile tile{lo, carry};
+                spread_pair<T, D, W>(sa, P, sc, tile, 0, s_cd.nf, plane);
             } else {
                 spread_pair<T, D, W>(sa, P, sc, DoubleTile{dv}, 0, s_cd.nf, plane);
             }
         }
         __syncthreads();
     }
-    if (cur >= 0) {
-        unsigned long long *g = sa.grid;
-        for (int e = threadIdx.x; e < ncell; e += blockDim.x) {
-            if constexpr (F32) {
-                const long long v = (long long)(((unsigned long long)(unsigned)hi[e] << 32) | lo[e]);
-                if (v && shift <= 62) atomicAdd(g + e, (unsigned long long)(v * (1ll << shift)));
-            } else {
-                const long long v = __double2ll_rn(dv[e] * ldexp(1.0, Eg));
-                if (v) atomicAdd(g + e, (unsigned long long)v);
-            }
-        }
-    }
+    if (cur >= 0) flush();
 }
 
 // One block per cell: Q = D(grid) - E(h) along every axis (Section 4.2).
@@ -569,6 +565,10 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
         set_error(PG_ERR_ARG, "upsampfac must be in [1.5, 4] (got %g)", o.upsampfac);
         return nullptr;
     }
+    if (o.angular_terms != 0) {
+        set_error(PG_ERR_ARG, "batched plans support VHS kernels only (angular_terms must be 0)");
+        return nullptr;
+    }
     for (int c = 0; c < ncell; ++c) {
         if (Ns[c] < 2 || Ns[c] > (o.d == 2 ? 200 : 40) || Ms[c] < 2 || Ms[c] % 2 || !(Ss[c] > 0.0) ||
             !(gammas[c] >= 0.0 && gammas[c] <= 1.0)) {
@@ -672,7 +672,9 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
         const long long cells_tile = (long long)ipow(cd.nf, d);
         cd.grid_off = grid_off;
         grid_off += cells_tile;
-        max_cells_tile = std::max<int>(max_cells_tile, (int)cells_tile);
+        // block tile: the last axis padded with unfolded columns (see spread_impl.cuh)
+        const long long tile_cells = (long long)ipow(cd.nf, d - 1) * (cd.nf + 2 * pgb::tile_col_pad(B->w));
+        max_cells_tile = std::max<int>(max_cells_tile, (int)tile_cells);
         cd.s_len = std::max<long long>(modes, (long long)(N + 1) * (long long)ipow(cd.nf, d - 1));
         cd.s_off = s_off;
         s_off += 4 * cd.s_len;
@@ -740,7 +742,7 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
         free_plan(p);
         return nullptr;
     }
-    B->spread_smem = (size_t)max_cells_tile * 8;
+    B->spread_smem = (size_t)max_cells_tile * (f32 ? 4 : 8);  // FP32: one word per cell; FP64: a double
     if (B->spread_smem + 1024 > prop.sharedMemPerBlockOptin) {
         set_error(PG_ERR_ARG, "largest cell's folded grid (%d cells) does not fit shared memory", max_cells_tile);
         free_plan(p);
@@ -759,6 +761,12 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
     }
     per_sm = std::min(per_sm, std::max(1, prop.maxThreadsPerMultiProcessor / B->spread_threads));
     B->spread_blocks = prop.multiProcessorCount * per_sm;
+    a.carry = nullptr;
+    a.carry_stride = max_cells_tile;
+    if (f32 && (rc = dev_alloc(p, (void **)&a.carry, (size_t)B->spread_blocks * max_cells_tile * sizeof(int)))) {
+        free_plan(p);
+        return nullptr;
+    }
     if ((rc = cuda_check(pgb::batch_spread_attr(f32, d, B->w, B->spread_smem), "batched spread attribute"))) {
         free_plan(p);
         return nullptr;

@@ -98,6 +98,8 @@ struct pg_boltz_plan_s {
     bool have_q = false;
     int last_launches = 0;
     pgb::SpreadArgs sargs{};   // spreading-kernel arguments (fixed at plan time)
+    pgb::Angular ang{};        // angular factor b(cos theta) of the collision kernel (n = 0: VHS)
+    double angmax = 1.0;       // bound of the even part of b on [-1, 1]
     // optional per-stage timing: events recorded on the plan's stream around the stages
     bool timing = false;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -119,6 +121,7 @@ struct pg_boltz_plan_s {
     double *a64 = nullptr;
     float *a32 = nullptr;
     double *h = nullptr, *Qplus = nullptr, *Qlast = nullptr, *mom = nullptr;
+    int *carry = nullptr;      // FP32 spreading: per-block carry counters
     double *ub = nullptr;      // N^d per-node strength bounds
     double *bound = nullptr;   // scalar B >= sum_p |q_p| (follows the grid in one allocation)
     unsigned long long *grid = nullptr;  // folded grid, int64 fixed point

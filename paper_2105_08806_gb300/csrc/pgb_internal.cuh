@@ -12,6 +12,14 @@ namespace pgb {
 
 // Everything the spreading kernel reads, passed by value.  The nodes, weights and
 // coefficients are in the kernel's arithmetic type T (float or double).
+// Angular factor of the collision kernel B(|g|, cos theta) = Bconst |g|^gamma b(cos theta)
+// (Eq. collision_form), b(c) = sum_{p < n} c_p c^p; n = 0 is the VHS kernel (b = 1).
+constexpr int kMaxAngular = 8;
+struct Angular {
+    int n;
+    double c[kMaxAngular];
+};
+
 struct SpreadArgs {
     int d, N, M, r;
     int nnode;            // N^d interior nodes
@@ -33,6 +41,15 @@ struct SpreadArgs {
     const double *tau;    // device scalar: node pairs whose strength bound is below it are skipped (0: none)
     unsigned long long *grid;  // nf^d folded grid, int64 fixed point in units of 2^-Eg
     int simple_fold;      // 1 when w <= n/2: unfolded indices lie in [-n/2, n] (no modulo needed)
+    int cpad;             // unfolded padding columns on each side of the last axis in block tiles
+    int ncol;             // nf + 2 cpad: tile cells along the last axis
+    int tile_cells;       // cells of one block tile (rows_per_slab rows)
+    int *carry;           // FP32: per-block carry counters, blocks x tile_cells (global memory)
+    // angular kernel: a spread pair stands for both orders, whose cos theta differ in sign, so
+    // the gain needs the even part b_e(c) = (b(c) + b(-c))/2 = sum_k ang_even[k] c^(2k) only
+    int nang_even;        // terms of ang_even; 0: VHS kernel (no angular factor)
+    double ang_even[kMaxAngular / 2];
+    double angmax;        // sum_k |ang_even[k]| >= |b_e(c)| on [-1, 1] (1 for VHS)
 };
 
 // Node pairs the spreading kernels walk: each unordered pair {i, j} once (the two orders add the
@@ -45,6 +62,11 @@ __host__ __device__ inline size_t spread_queue_bytes(int threads, int d, size_t 
 {
     return (size_t)(threads / 32) * 32 * (d + 1) * elem;
 }
+
+// Padding columns of the block tiles' last axis for kernel width w: the unfolded support of a point
+// at grid coordinate x in [0, n/2] spans floor(x - w/2) + 1 .. floor(x + w/2), i.e. at most w/2
+// columns beyond either end; w/2 + 1 leave a margin for rounding of x.
+__host__ __device__ inline int tile_col_pad(int w) { return w / 2 + 1; }
 
 // Exponent Eg of the grid's fixed-point unit 2^-Eg: the largest E with B 2^E < 2^61 for the
 // bound B >= sum_p |q_p| (0 when B is zero or not finite).
@@ -65,6 +87,11 @@ cudaError_t launch_spread_f32_d2(const SpreadArgs &a, int w, int blocks, int thr
 cudaError_t launch_spread_f32_d3(const SpreadArgs &a, int w, int blocks, int threads, size_t smem, cudaStream_t s);
 cudaError_t launch_spread_f64_d2(const SpreadArgs &a, int w, int blocks, int threads, size_t smem, cudaStream_t s);
 cudaError_t launch_spread_f64_d3(const SpreadArgs &a, int w, int blocks, int threads, size_t smem, cudaStream_t s);
+// The same with the angular factor of the collision kernel (a.nang_even > 0; called by the above).
+cudaError_t launch_spread_f32_d2_ang(const SpreadArgs &a, int w, int blocks, int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_spread_f32_d3_ang(const SpreadArgs &a, int w, int blocks, int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_spread_f64_d2_ang(const SpreadArgs &a, int w, int blocks, int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_spread_f64_d3_ang(const SpreadArgs &a, int w, int blocks, int threads, size_t smem, cudaStream_t s);
 // Highest kernel width with a compiled spreading kernel for each type.
 constexpr int kMaxWidthF32 = 10;
 constexpr int kMaxWidthF64 = 16;
@@ -85,13 +112,17 @@ cudaError_t launch_axis_pass(const double *in, Dims3 in_dims, int ax, const doub
 // writes a (FP64) and, if af != nullptr, a float copy.
 cudaError_t launch_recon_last(const double *in, Dims3 in_dims, const double *A, int m,
                               const double *scale, int d, double *a, float *af, cudaStream_t s);
-// Loss: h_i = a_i * Lsum_i * prod_l inv_mu2[i_l], Lsum_i = Bw * sum_j a_j B(|v_i - v_j|);
-// also ub_i = |a_i| Bw sum_j |a_j| B_ij prod_l mu^-2(|c_l| + rad), an upper bound of the
+// Loss: h_i = a_i * Lsum_i * prod_l inv_mu2[i_l], Lsum_i = Bw * sum_j a_j B(|v_i - v_j|) A_ij,
+// A_ij = (1/Wsig) sum_m w_m b(cos theta_ijm) for an angular kernel (ang.n > 0; the sum over the
+// sphere set then runs per pair), 1 otherwise (Bw = Bconst Wsig);
+// also ub_i = |a_i| Bw angmax sum_j |a_j| B_ij prod_l mu^-2(|c_l| + rad), an upper bound of the
 // spreading strengths of the pairs (i, .).  FP32 pair terms carry a relative error near 1e-7,
 // well inside the FP32 path's tolerance; the bound gets a 1e-5 margin in k_bound_reduce.
 // vnode32 != nullptr selects FP32 pair terms (the FP32 path).
 // hist != nullptr: also count every pair bound |a_i| Bw |a_j| B_ij prod mu^-2 into the screening histogram.
-cudaError_t launch_loss(const double *a, const double *vnode, const float *vnode32, int N, int d, double gamma,
+cudaError_t launch_loss(const double *a, const double *vnode, const float *vnode32, int N, int d, int M,
+                        const double *sig, const double *wsig, const float *sig32, const float *wsig32,
+                        const Angular &ang, double angmax, double Wsig, double gamma,
                         int fast_gamma, double Bw, const double *inv_mu2, double S, int r,
                         double *h, double *ub, unsigned long long *hist, cudaStream_t s);
 // Screening bin of a pair bound u > 0.
@@ -119,8 +150,8 @@ cudaError_t launch_rk4_update(double *f, const double *k1, const double *k2, con
                               double dt, long long n, cudaStream_t s);
 // Discrete weak-form functionals and scales for phi in {1, v_l, |v|^2}, added into out[2(d+2)].
 cudaError_t launch_weak_moments(const double *a, const double *vnode, int N, int d, int M, const double *sig,
-                                const double *wsig, double gamma, int fast_gamma, double Bconst, double *out,
-                                cudaStream_t s);
+                                const double *wsig, const Angular &ang, double gamma, int fast_gamma, double Bconst,
+                                double *out, cudaStream_t s);
 // Diagnostics: mass/energy functionals of Q and Qplus and their L2 norms into out[6].
 cudaError_t launch_moments(const double *Q, const double *Qplus, int d, int N, double S,
                            double *out, cudaStream_t s);

@@ -34,6 +34,13 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
     p->npairs = pgb::unordered_pairs(p->nnode);
     p->fast_gamma = (p->gamma == 0.0) ? 0 : (p->gamma == 1.0) ? 1 : (p->gamma == 0.5) ? 2 : 3;
     p->Bconst = 1.0 / (d == 2 ? 2.0 * kPi : 4.0 * kPi);
+    p->ang.n = o.angular_terms;
+    for (int t = 0; t < o.angular_terms; ++t) p->ang.c[t] = o.angular_coef[t];
+    p->angmax = 1.0;
+    if (p->ang.n) {
+        p->angmax = 0.0;
+        for (int t = 0; t < p->ang.n; t += 2) p->angmax += std::fabs(p->ang.c[t]);
+    }
 
     // ---- transform / spreading parameters
     p->sigma_up = (o.upsampfac > 0.0) ? o.upsampfac : 2.0;
@@ -104,8 +111,10 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
     cudaDeviceProp prop;
     cudaError_t e = cudaGetDeviceProperties(&prop, p->device);
     if (e != cudaSuccess) return set_error(PG_ERR_CUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e));
-    const size_t elem = 8;  // two 32-bit words per cell (64-bit fixed point), both precisions
-    const size_t plane = (size_t)nfd1;
+    const size_t elem = (p->prec == PG_PREC_FP32) ? 4 : 8;  // FP32: one 32-bit word per cell; FP64: a double
+    // block tiles: rows of (nf^(d-2) x ncol) cells, the last axis padded with unfolded columns
+    const int cpad = pgb::tile_col_pad(p->w), ncol = p->nf + 2 * cpad;
+    const size_t plane = (size_t)ipow(p->nf, d - 2) * ncol;
     const size_t max_smem = prop.sharedMemPerBlockOptin - 1024;  // leave room for the kernels' static shared memory
     const bool f32 = (p->prec == PG_PREC_FP32);
     const int max_threads = f32 ? pgb::kMaxThreadsF32 : pgb::kMaxThreadsF64;
@@ -127,8 +136,13 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
     per_sm = std::max(per_sm, 1);
     if (o.spread_threads > 0) {
         p->spread_threads = o.spread_threads;
+    } else if (f32) {
+        // FP32: one block of 1024 threads per SM (measured fastest; more, smaller blocks
+        // multiply the tile clears and flushes)
+        p->spread_threads = max_threads;
+        per_sm = 1;
     } else {
-        // about 1024 resident threads per SM (the kernels use up to 64 registers)
+        // about 1024 resident threads per SM
         int t = (1024 / per_sm) / 32 * 32;
         p->spread_threads = std::max(128, std::min(max_threads, t));
     }
@@ -145,6 +159,11 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
     const long long need = ((p->npairs + p->spread_threads - 1) / p->spread_threads) * p->nslab;
     blocks = std::min(blocks, need);
     p->spread_blocks = (int)blocks;
+    const long long tile_cells = (long long)p->rows_per_slab * (long long)plane;
+    if (f32) {  // per-block carry counters of the FP32 tiles (global memory, cleared by each block)
+        int rc2 = dev_alloc(p, (void **)&p->carry, (size_t)blocks * tile_cells * sizeof(int));
+        if (rc2) return rc2;
+    }
 
     // ---- spreading-kernel arguments
     pgb::SpreadArgs &ka = p->sargs;
@@ -174,6 +193,13 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
     ka.tau = p->tau;
     ka.grid = p->grid;
     ka.simple_fold = (p->w <= p->n / 2) ? 1 : 0;
+    ka.cpad = cpad;
+    ka.ncol = ncol;
+    ka.tile_cells = (int)tile_cells;
+    ka.carry = p->carry;
+    ka.nang_even = p->ang.n ? (p->ang.n + 1) / 2 : 0;
+    for (int k = 0; k < ka.nang_even; ++k) ka.ang_even[k] = p->ang.c[2 * k];
+    ka.angmax = p->angmax;
     return PG_OK;
 }
 
@@ -193,6 +219,13 @@ int validate(const pg_boltz_opts_t &o)
         return set_error(PG_ERR_ARG, "upsampfac must be in [1.5, 4] (got %g)", o.upsampfac);
     if (o.proj_nodes < 0 || o.proj_nodes > 4096) return set_error(PG_ERR_ARG, "proj_nodes out of range");
     if (o.screen != 0 && o.screen != 1) return set_error(PG_ERR_ARG, "screen must be 0 or 1");
+    if (o.angular_terms < 0 || o.angular_terms > pgb::kMaxAngular)
+        return set_error(PG_ERR_ARG, "angular_terms must be in [0, %d] (got %d)", pgb::kMaxAngular, o.angular_terms);
+    if (o.angular_terms > 0) {
+        if (!o.angular_coef) return set_error(PG_ERR_ARG, "angular_coef is NULL");
+        for (int t = 0; t < o.angular_terms; ++t)
+            if (!std::isfinite(o.angular_coef[t])) return set_error(PG_ERR_ARG, "angular_coef[%d] is not finite", t);
+    }
     return PG_OK;
 }
 
@@ -336,7 +369,8 @@ PG_API int pg_boltz_collide(pg_boltz_plan_t *p, const double *f_dev, double *Q_d
                          "memset grid")))
         return rc;
     ++launches;
-    if ((rc = cuda_check(pgb::launch_loss(p->a64, p->v64, f32 ? p->v32 : nullptr, N, d, p->gamma, p->fast_gamma,
+    if ((rc = cuda_check(pgb::launch_loss(p->a64, p->v64, f32 ? p->v32 : nullptr, N, d, p->M, p->sig64, p->wsig64,
+                                          p->sig32, p->wsig32, p->ang, p->angmax, p->Wsig, p->gamma, p->fast_gamma,
                                           p->Bconst * p->Wsig, p->inv_mu2, p->S, p->r, p->h, p->ub,
                                           p->screen_eps > 0.0 ? p->hist : nullptr, p->stream),
                          "loss")))
@@ -473,8 +507,8 @@ PG_API int pg_boltz_conservation(pg_boltz_plan_t *p, const double *f_dev, double
         return rc;
     const int nout = 2 * (d + 2);
     if ((rc = cuda_check(cudaMemsetAsync(p->mom, 0, nout * sizeof(double), p->stream), "memset"))) return rc;
-    if ((rc = cuda_check(pgb::launch_weak_moments(p->a64, p->v64, N, d, p->M, p->sig64, p->wsig64, p->gamma,
-                                                  p->fast_gamma, p->Bconst, p->mom, p->stream),
+    if ((rc = cuda_check(pgb::launch_weak_moments(p->a64, p->v64, N, d, p->M, p->sig64, p->wsig64, p->ang,
+                                                  p->gamma, p->fast_gamma, p->Bconst, p->mom, p->stream),
                          "weak moments")))
         return rc;
     double tmp[10];

@@ -1,4 +1,5 @@
-// Spreading kernels for d = 2: FP32 point generation and int32 fixed-point shared-memory accumulation.
+// Spreading kernels for d = 2, VHS kernels: FP32 point generation and split 64-bit fixed-point shared-memory accumulation.
+// Angular kernels B(|g|, cos theta) use the instantiations of spread_f32_2d_ang.cu.
 #include "spread_impl.cuh"
 
 namespace pgb {
@@ -6,7 +7,8 @@ namespace pgb {
 cudaError_t launch_spread_f32_d2(const SpreadArgs &a, int w, int blocks, int threads, size_t smem,
                                   cudaStream_t s)
 {
-    return spread_detail::WidthDispatch<true, 2, kMinWidth, kMaxWidthF32>::run(a, w, blocks, threads, smem, s);
+    if (a.nang_even) return launch_spread_f32_d2_ang(a, w, blocks, threads, smem, s);
+    return spread_detail::WidthDispatch<true, 2, kMinWidth, kMaxWidthF32, false>::run(a, w, blocks, threads, smem, s);
 }
 
 }  // namespace pgb

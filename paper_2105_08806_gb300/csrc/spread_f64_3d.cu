@@ -1,4 +1,5 @@
-// Spreading kernels for d = 3: FP64 point generation and int64 fixed-point shared-memory accumulation.
+// Spreading kernels for d = 3, VHS kernels: FP64 point generation and FP64 shared-memory partial sums.
+// Angular kernels B(|g|, cos theta) use the instantiations of spread_f64_3d_ang.cu.
 #include "spread_impl.cuh"
 
 namespace pgb {
@@ -6,7 +7,8 @@ namespace pgb {
 cudaError_t launch_spread_f64_d3(const SpreadArgs &a, int w, int blocks, int threads, size_t smem,
                                   cudaStream_t s)
 {
-    return spread_detail::WidthDispatch<false, 3, kMinWidth, kMaxWidthF64>::run(a, w, blocks, threads, smem, s);
+    if (a.nang_even) return launch_spread_f64_d3_ang(a, w, blocks, threads, smem, s);
+    return spread_detail::WidthDispatch<false, 3, kMinWidth, kMaxWidthF64, false>::run(a, w, blocks, threads, smem, s);
 }
 
 }  // namespace pgb

@@ -25,18 +25,14 @@
 //  - FP64 kernel: each block adds into a private FP64 copy of its slab of the grid in shared
 //    memory; at the end each cell's partial sum is rounded to the grid unit (relative error
 //    2^-61 B) and added to the global grid.
-//  - FP32 kernel: the private copy is 64-bit fixed point kept as two 32-bit words per cell
-//    (lo, unsigned; hi, signed) in units of 2^-Et, Et = Eg - 10:
-//    a contribution x (int64) is added to lo with one native 32-bit shared atomic; the
-//    carry of that addition (from the returned old value) plus the high half of x goes to
-//    hi with a second atomic only when it is non-zero.  The unit is chosen so typical
-//    contributions fit in ~22 bits, so the second atomic is rare.  Atomic additions on lo are
-//    serialised, so every carry is the carry of exactly that addition and hi:lo ends as the
-//    exact two's-complement sum.  (Floating-point shared atomics are compare-and-swap loops
-//    and their rounding limits FP32 accuracy; 64-bit integer shared atomics are several
-//    times slower than 32-bit ones.)
-//    At the end each block adds its slab (hi:lo scaled by 2^10) to the global grid.  Each
-//    contribution is rounded once, to the tile unit; all later additions are exact.
+//  - FP32 kernel: the private copy holds one signed 32-bit fixed-point word per cell in units of
+//    2^-Et, Et = Eg - kTileBits (SplitTile): a contribution goes to its word with one native
+//    32-bit shared atomic, and only an addition that overflows the word's signed range (seen
+//    from the returned old value) sends the wrapped 2^32 units to the cell's int64 entry of the
+//    global grid.  (Floating-point shared atomics are compare-and-swap loops and their rounding
+//    limits FP32 accuracy; 64-bit integer shared atomics are several times slower than 32-bit
+//    ones.)  At the end each block adds its words (scaled by 2^kTileBits) to the global grid.
+//    Each contribution is rounded once, to the tile unit; all later additions are exact.
 #pragma once
 
 #include <climits>
@@ -94,28 +90,38 @@ __device__ __forceinline__ int fold_cell(int u, int n, bool simple)
 }
 
 // The w kernel weights psi(x_u - z) of one axis, u = s..s+w-1, in units where one grid cell
-// is 1 and x = z n / (2 pi): psi = exp(beta (sqrt(1 - t^2) - 1)), t = (u - x) 2/w.
+// is 1 and x = z n / (2 pi): psi = exp(beta (sqrt(1 - t^2) - 1)), t = (u - x) 2/w.  Returns
+// the first unfolded index s.
 template <int W>
-__device__ __forceinline__ void axis_weights_f32(const SpreadArgs &p, float x, float *wt, int *idx);
+__device__ __forceinline__ int kernel_weights_f32(const SpreadArgs &p, float x, float *wt);
 
+template <typename T, int W>
+__device__ __forceinline__ int kernel_weights(const SpreadArgs &p, T x, T *wt)
+{
+    if constexpr (sizeof(T) == 4) {
+        return kernel_weights_f32<W>(p, x, wt);
+    } else {
+        const int s = (int)Fn<T>::floor_(x - T(0.5 * W)) + 1;
+        const T inv_hw = T(2.0 / W);
+        const T beta = T(p.beta);
+#pragma unroll
+        for (int a = 0; a < W; ++a) {
+            const T t = (T(s + a) - x) * inv_hw;
+            const T one_m = T(1) - t * t;
+            wt[a] = one_m > T(0) ? Fn<T>::exp_(beta * (Fn<T>::sqrt_pos(one_m) - T(1))) : T(0);
+        }
+        return s;
+    }
+}
+
+// The weights and the folded cells fold(s + a) of one axis.
 template <typename T, int W>
 __device__ __forceinline__ void axis_weights(const SpreadArgs &p, T x, T *wt, int *idx)
 {
-    if constexpr (sizeof(T) == 4) {
-        axis_weights_f32<W>(p, x, wt, idx);
-        return;
-    }
-    const int s = (int)Fn<T>::floor_(x - T(0.5 * W)) + 1;
-    const T inv_hw = T(2.0 / W);
-    const T beta = T(p.beta);
+    const int s = kernel_weights<T, W>(p, x, wt);
     const bool simple = p.simple_fold != 0;
 #pragma unroll
-    for (int a = 0; a < W; ++a) {
-        const T t = (T(s + a) - x) * inv_hw;
-        const T one_m = T(1) - t * t;
-        wt[a] = one_m > T(0) ? Fn<T>::exp_(beta * (Fn<T>::sqrt_pos(one_m) - T(1))) : T(0);
-        idx[a] = fold_cell(s + a, p.n, simple);
-    }
+    for (int a = 0; a < W; ++a) idx[a] = fold_cell(s + a, p.n, simple);
 }
 
 __device__ __forceinline__ float ex2_approx(float x)
@@ -179,47 +185,20 @@ __device__ __forceinline__ void angle_weight_f32(float v, float S, float invS, b
 // FP32 weights: t_a = (s - x) 2/w + a 2/w, psi = 2^(beta log2(e) (sqrt(1 - t^2) - 1)), with the
 // square root as (1 - t^2) rsqrt(1 - t^2); both approximations are good to a few 1e-7.
 template <int W>
-__device__ __forceinline__ void axis_weights_f32(const SpreadArgs &p, float x, float *wt, int *idx)
+__device__ __forceinline__ int kernel_weights_f32(const SpreadArgs &p, float x, float *wt)
 {
     const int s = (int)floorf(x - 0.5f * W) + 1;
     const float h2 = 2.0f / W;
     const float t0 = ((float)s - x) * h2;
     const float bl = (float)(p.beta * 1.4426950408889634);
-    const bool simple = p.simple_fold != 0;
 #pragma unroll
     for (int a = 0; a < W; ++a) {
         const float t = t0 + (float)a * h2;
         const float om = fmaf(-t, t, 1.0f);
         const float e = fmaf(bl, om * rsqrt_approx(om), -bl);
         wt[a] = om > 0.0f ? ex2_approx(e) : 0.0f;
-        idx[a] = fold_cell(s + a, p.n, simple);
     }
-}
-
-// Add one contribution x (already in tile units) to cell c of the split tile.
-__device__ __forceinline__ void add_split(unsigned *lo, int *hi, int c, long long x)
-{
-    if (x == 0) return;
-    const unsigned xl = (unsigned)x;
-    const unsigned old = atomicAdd(lo + c, xl);
-    const int carry = (old + xl < old) ? 1 : 0;
-    const int h = (int)(x >> 32) + carry;
-    if (h) atomicAdd(hi + c, h);
-}
-// FP32 contribution -> split tile: most contributions fit in 31 bits (the 32-bit conversion is
-// cheaper); larger ones take the 64-bit conversion.  Zero contributions are added too: a
-// branch around them costs more than the atomic.
-__device__ __forceinline__ void add_contrib(unsigned *lo, int *hi, int c, float x)
-{
-    if (fabsf(x) < 2147483648.0f) {
-        const int v = __float2int_rn(x);
-        const unsigned xl = (unsigned)v;
-        const unsigned old = atomicAdd(lo + c, xl);
-        const int h = ((v < 0) ? -1 : 0) + ((old + xl < old) ? 1 : 0);
-        if (h) atomicAdd(hi + c, h);
-    } else {
-        add_split(lo, hi, c, __float2ll_rn(x));
-    }
+    return s;
 }
 
 template <typename T, int D>
@@ -228,6 +207,7 @@ struct PairData {
     T rad;     // |v_i - v_j|/2
     T base;    // a_i a_j B(|v_i - v_j|)
     T mult;    // 2 for i != j (the pair stands for (i, j) and (j, i)), 1 for i == j
+    T dir[D];  // (v_i - v_j)/|v_i - v_j| (0 for i == j): cos theta = dir . sigma_m
 };
 
 // Unordered node pairs.  Swapping i and j keeps the centre (v_i + v_j)/2, the radius
@@ -237,8 +217,8 @@ struct PairData {
 // t = 0 is the diagonal (multiplicity 1) and, for even nnode, the row t = nnode/2 stops at
 // i = nnode/2 - 1 (its other half repeats the same pairs): unordered_pairs(nnode) in all.
 
-// Load pair pr; false when its strength is zero.
-template <typename T, int D>
+// Load pair pr; false when its strength is zero.  ANG: also the unit direction (angular kernels).
+template <typename T, int D, bool ANG = false>
 __device__ __forceinline__ bool load_pair(const SpreadArgs &p, long long pr, PairData<T, D> &P)
 {
     const int nnode = p.nnode, N = p.N;
@@ -261,8 +241,14 @@ __device__ __forceinline__ bool load_pair(const SpreadArgs &p, long long pr, Pai
         const T dl = vi - vj;
         g2 += dl * dl;
         P.cen[l] = T(0.5) * (vi + vj);
+        if constexpr (ANG) P.dir[l] = dl;
     }
     const T g = Fn<T>::sqrt_(g2);
+    if constexpr (ANG) {
+        const T ginv = g > T(0) ? T(1) / g : T(0);
+#pragma unroll
+        for (int l = 0; l < D; ++l) P.dir[l] *= ginv;
+    }
     T B;
     switch (p.fast_gamma) {
     case 0: B = T(p.Bconst); break;
@@ -281,7 +267,7 @@ template <typename T, int D>
 __device__ __forceinline__ T pair_bound(const SpreadArgs &p, const PairData<T, D> &P)
 {
     const T S = T(p.S), invS = T(1) / S;
-    T U = fabs(P.base) * T(p.Wsig);
+    T U = fabs(P.base) * T(p.Wsig * p.angmax);
 #pragma unroll
     for (int l = 0; l < D; ++l) {
         const T R = fabs(P.cen[l]) + P.rad;
@@ -290,21 +276,54 @@ __device__ __forceinline__ T pair_bound(const SpreadArgs &p, const PairData<T, D
     return U;
 }
 
-// Spread the M points of one pair into the block tile; `sc` converts to tile units.
+// Global folded-grid cell of tile cell c (tile layout: see spread_point) in a tile whose first row is row_lo.
+__device__ __forceinline__ int tile_to_grid_cell(int c, int D, int nf, int ncol, int cpad, int n, int row_lo)
+{
+    const int u = c % ncol - cpad;
+    const int rest = c / ncol;  // row (2D) or row nf + j (3D), relative to row_lo
+    return (row_lo * (D == 3 ? nf : 1) + rest) * nf + fold_index(u, n);
+}
+
 // Shared-memory accumulators of the block tile.
-struct SplitTile {  // FP32 path: 64-bit fixed point as (lo, hi) 32-bit words
-    unsigned *lo;
-    int *hi;
-    __device__ __forceinline__ void add(int c, float x) const { add_contrib(lo, hi, c, x); }
-    // |x| < 2^31 known for the whole pair: the high word takes the sign and the carry, which
-    // cancel for most negative contributions
-    __device__ __forceinline__ void add_small(int c, float x) const
+//
+// FP32 path: one signed 32-bit fixed-point word per cell in shared memory, in units 2^-Et of the
+// tile (Et = Eg - kTileBits), plus a per-block carry array of the same layout in global memory.
+// A contribution v in [-2^31, 2^31) goes to its word with one native 32-bit atomic; when that
+// addition overflows the signed range (visible from the returned old value o and the result r:
+// (o ^ r) & (v ^ r) < 0) the wrapped +-1 x 2^32 tile units go to the cell's carry counter.
+// Atomic additions on a word are serialised, so every wrap is that of exactly one addition and
+// word + 2^32 carry is the exact sum in any order.  Contributions of 2^31 units or more split
+// into a word part and a multiple of 2^32 added to the carry directly.  A block's partial sum in
+// one cell stays below B 2^Et = 2^(61 - kTileBits), so carries are rare (about B 2^Et / 2^32
+// in a whole evaluation) and a counter stays below 2^(29 - kTileBits) in magnitude.
+constexpr int kTileBits = 14;
+
+struct SplitTile {
+    int *lo;     // tile words (shared memory)
+    int *carry;  // this block's carry counters (global memory, same layout)
+    __device__ __forceinline__ void add32(int c, int v) const
     {
-        const int v = __float2int_rn(x);
-        const unsigned old = atomicAdd(lo + c, (unsigned)v);
-        const int h = (v >> 31) + ((old + (unsigned)v < old) ? 1 : 0);
-        if (h) atomicAdd(hi + c, h);
+        const int o = atomicAdd(lo + c, v);
+        const int r = (int)((unsigned)o + (unsigned)v);
+        if (((o ^ r) & (v ^ r)) < 0) atomicAdd(carry + c, v < 0 ? -1 : 1);
     }
+    __device__ __forceinline__ void add64(int c, long long x) const
+    {
+        const int xl = (int)(unsigned)(unsigned long long)x;  // low word, signed
+        const long long xh = (x - xl) >> 32;                   // exact: x - xl is a multiple of 2^32
+        add32(c, xl);
+        if (xh) atomicAdd(carry + c, (int)xh);
+    }
+    // Zero contributions are added too: a branch around them costs more than the atomic.
+    __device__ __forceinline__ void add(int c, float x) const
+    {
+        if (fabsf(x) < 2147483648.0f) add32(c, __float2int_rn(x));
+        else add64(c, __float2ll_rn(x));
+    }
+    // |x| < 2^31 known in advance
+    __device__ __forceinline__ void add_small(int c, float x) const { add32(c, __float2int_rn(x)); }
+    // the cell's sum in tile units
+    __device__ __forceinline__ long long value(int c) const { return (long long)carry[c] * 4294967296LL + lo[c]; }
 };
 struct DoubleTile {  // FP64 path: FP64 partial sums
     double *v;
@@ -317,7 +336,7 @@ struct DoubleTile {  // FP64 path: FP64 partial sums
 
 // Point m of pair P: grid coordinates x (one grid cell = 1, x = z n / (2 pi)) and strength q in
 // tile units (qbase = a_i a_j B x multiplicity x tile scale).
-template <typename T, int D>
+template <typename T, int D, bool ANG = false>
 __device__ __forceinline__ void make_point(const SpreadArgs &p, const PairData<T, D> &P, T qbase, int m, T *x, T &q)
 {
     const T *sig = static_cast<const T *>(p.sig);
@@ -326,6 +345,15 @@ __device__ __forceinline__ void make_point(const SpreadArgs &p, const PairData<T
     const T gs = T(p.grid_scale);
     const bool alg = (p.r == 1);
     q = qbase * wsig[m];
+    if constexpr (ANG) {  // even part of b(cos theta), Horner in cos^2 theta
+        T c = T(0);
+#pragma unroll
+        for (int l = 0; l < D; ++l) c += P.dir[l] * sig[m * D + l];
+        const T c2 = c * c;
+        T be = T(p.ang_even[p.nang_even - 1]);
+        for (int k = p.nang_even - 2; k >= 0; --k) be = be * c2 + T(p.ang_even[k]);
+        q *= be;
+    }
 #pragma unroll
     for (int l = 0; l < D; ++l) {
         const T vp = P.cen[l] + P.rad * sig[m * D + l];
@@ -345,15 +373,21 @@ __device__ __forceinline__ void make_point(const SpreadArgs &p, const PairData<T
     }
 }
 
-// Add the w^d contributions of one point to the rows row_lo..row_lo+nrows-1 of the block tile.
-// SMALL: every contribution is known to lie in (-2^31, 2^31) tile units, so the tile's cheaper
-// add_small applies.  SLAB: the tile holds a slab of the grid's rows and rows outside it are
-// skipped; otherwise it holds every row (row_lo = 0, nrows = n/2 + 1).
+// Tile layout.  A block tile holds rows row_lo..row_lo+nrows-1 of axis 0 of the folded grid, and
+// along the last axis it keeps the UNFOLDED columns u = -cpad..nf-1+cpad at u + cpad (ncol =
+// nf + 2 cpad cells): the w columns of a point are then consecutive, with no folding and no
+// per-contribution index arithmetic.  The padding columns are folded onto their cells when the
+// tile is added to the global grid (tile_to_grid_cell).  2D cell (row, u): row ncol + u + cpad;
+// 3D cell (row, j, u): (row nf + j) ncol + u + cpad.
+
+// Add the w^d contributions of one point to the block tile.  SMALL: every contribution is known
+// to lie in (-2^31, 2^31) tile units, so the tile's cheaper add_small applies.  SLAB: the tile
+// holds a slab of the grid's rows and rows outside it are skipped; otherwise it holds every row
+// (row_lo = 0, nrows = n/2 + 1).
 template <typename T, int D, int W, typename Tile, bool SMALL, bool SLAB>
 __device__ __forceinline__ void spread_point(const SpreadArgs &p, const T *x, T q, const Tile &tile, int row_lo,
                                              int nrows, int plane)
 {
-    const int nf = p.nf;
     T w0[W];
     int r0[W];
     axis_weights<T, W>(p, x[0], w0, r0);
@@ -367,26 +401,25 @@ __device__ __forceinline__ void spread_point(const SpreadArgs &p, const T *x, T 
         w0[a] *= q;
     }
     if (!hit) return;
-    T w1[W];
-    int c1[W];
-    axis_weights<T, W>(p, x[1], w1, c1);
+    T wl[W];  // last axis: consecutive padded columns cb..cb+w-1 (clamped: x lies in [0, n/2])
+    const int cb = min(max(kernel_weights<T, W>(p, x[D - 1], wl) + p.cpad, 0), p.ncol - W);
     if (D == 2) {
 #pragma unroll
         for (int a = 0; a < W; ++a) {
             if (SLAB && (unsigned)r0[a] >= (unsigned)nrows) continue;
-            const int row = r0[a] * plane;
+            const int row = r0[a] * plane + cb;
 #pragma unroll
-            for (int b = 0; b < W; ++b) {
-                if constexpr (SMALL) tile.add_small(row + c1[b], w0[a] * w1[b]);
-                else tile.add(row + c1[b], w0[a] * w1[b]);
+            for (int c = 0; c < W; ++c) {
+                if constexpr (SMALL) tile.add_small(row + c, w0[a] * wl[c]);
+                else tile.add(row + c, w0[a] * wl[c]);
             }
         }
     } else {
-        T w2[W];
-        int c2[W];
-        axis_weights<T, W>(p, x[D - 1], w2, c2);
+        T w1[W];
+        int c1[W];
+        axis_weights<T, W>(p, x[1], w1, c1);
 #pragma unroll
-        for (int b = 0; b < W; ++b) c1[b] *= nf;
+        for (int b = 0; b < W; ++b) c1[b] = c1[b] * p.ncol + cb;
         for (int a = 0; a < W; ++a) {
             if (SLAB && (unsigned)r0[a] >= (unsigned)nrows) continue;
             const int row = r0[a] * plane;
@@ -396,23 +429,24 @@ __device__ __forceinline__ void spread_point(const SpreadArgs &p, const T *x, T 
                 const int line = row + c1[b];
 #pragma unroll
                 for (int c = 0; c < W; ++c) {
-                    if constexpr (SMALL) tile.add_small(line + c2[c], wab * w2[c]);
-                    else tile.add(line + c2[c], wab * w2[c]);
+                    if constexpr (SMALL) tile.add_small(line + c, wab * wl[c]);
+                    else tile.add(line + c, wab * wl[c]);
                 }
             }
         }
     }
 }
 
+
 // The M points of one pair, into a tile that holds every row of the grid.
-template <typename T, int D, int W, typename Tile, bool SMALL>
+template <typename T, int D, int W, typename Tile, bool SMALL, bool ANG>
 __device__ __forceinline__ void spread_points(const SpreadArgs &p, const PairData<T, D> &P, T sc, const Tile &tile,
                                               int row_lo, int nrows, int plane)
 {
     const T qbase = P.base * sc;
     for (int m = 0; m < p.M; ++m) {
         T x[D], q;
-        make_point<T, D>(p, P, qbase, m, x, q);
+        make_point<T, D, ANG>(p, P, qbase, m, x, q);
         spread_point<T, D, W, Tile, SMALL, false>(p, x, q, tile, row_lo, nrows, plane);
     }
 }
@@ -420,17 +454,17 @@ __device__ __forceinline__ void spread_points(const SpreadArgs &p, const PairDat
 // Spread the M points of one pair into the block tile; `sc` converts to tile units.  Pairs
 // whose largest single contribution is bounded below 2^30 tile units in magnitude (pair bound
 // x max_m w_m / sum_m w_m, kernel weights <= 1) take the SMALL path.
-template <typename T, int D, int W, typename Tile>
+template <typename T, int D, int W, typename Tile, bool ANG = false>
 __device__ __forceinline__ void spread_pair(const SpreadArgs &p, const PairData<T, D> &P, T sc, const Tile &tile,
                                             int row_lo, int nrows, int plane)
 {
     if constexpr (sizeof(T) == 4) {
         if (pair_bound<T, D>(p, P) * sc * T(p.wmax_frac) < T(1073741824.0f)) {
-            spread_points<T, D, W, Tile, true>(p, P, sc, tile, row_lo, nrows, plane);
+            spread_points<T, D, W, Tile, true, ANG>(p, P, sc, tile, row_lo, nrows, plane);
             return;
         }
     }
-    spread_points<T, D, W, Tile, false>(p, P, sc, tile, row_lo, nrows, plane);
+    spread_points<T, D, W, Tile, false, ANG>(p, P, sc, tile, row_lo, nrows, plane);
 }
 
 // ---- slabbed grids: warp point queues
@@ -487,7 +521,7 @@ __device__ __forceinline__ void queue_spread(const SpreadArgs &p, const T *buf, 
 
 // The pairs pr = first, first + nthr, ... of one thread, spread into one slab through the
 // warp's queue `buf` ((D + 1) x 32 values).  Every loop condition is uniform over the warp.
-template <typename T, int D, int W, typename Tile>
+template <typename T, int D, int W, typename Tile, bool ANG>
 __device__ __forceinline__ void spread_pairs_queued(const SpreadArgs &p, long long first, long long nthr, T sc, T tau,
                                                     const Tile &tile, int row_lo, int nrows, int plane, T *buf)
 {
@@ -497,7 +531,7 @@ __device__ __forceinline__ void spread_pairs_queued(const SpreadArgs &p, long lo
     int count = 0;  // queued points, the same in every lane
     for (long long pr = first; __any_sync(full, pr < p.npairs); pr += nthr) {
         PairData<T, D> P;
-        bool ok = pr < p.npairs && load_pair<T, D>(p, pr, P);
+        bool ok = pr < p.npairs && load_pair<T, D, ANG>(p, pr, P);
         if (ok && tau > T(0) && pair_bound<T, D>(p, P) < tau) ok = false;
         if (!__any_sync(full, ok)) continue;
         const T qbase = ok ? P.base * P.mult * sc : T(0);
@@ -505,7 +539,7 @@ __device__ __forceinline__ void spread_pairs_queued(const SpreadArgs &p, long lo
             T x[D], q = T(0);
             bool hit = false;
             if (ok) {
-                make_point<T, D>(p, P, qbase, m, x, q);
+                make_point<T, D, ANG>(p, P, qbase, m, x, q);
                 hit = rows_hit<T, W>(p, x[0], row_lo, nrows);
             }
             const unsigned mask = __ballot_sync(full, hit);
@@ -533,7 +567,7 @@ struct SlabGeom {
 __device__ __forceinline__ SlabGeom slab_geometry(const SpreadArgs &p, int D)
 {
     SlabGeom g;
-    g.plane = (D == 3) ? p.nf * p.nf : p.nf;
+    g.plane = (D == 3) ? p.nf * p.ncol : p.ncol;
     const int slab = blockIdx.x % p.nslab;
     g.row_lo = slab * p.rows_per_slab;
     const int row_hi = min(g.row_lo + p.rows_per_slab, p.nf);
@@ -555,51 +589,55 @@ __device__ __forceinline__ void pair_schedule(const SpreadArgs &p, long long &fi
     first = (long long)(threadIdx.x & 31) * nwarps + gwarp;
 }
 
-template <int D, int W>
+template <int D, int W, bool ANG>
 __global__ void __launch_bounds__(kMaxThreadsF32) k_spread_f32(const __grid_constant__ SpreadArgs p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SlabGeom G = slab_geometry(p, D);
     if (G.nrows <= 0) return;  // uniform over the block: an empty trailing slab does nothing
-    SplitTile tile{reinterpret_cast<unsigned *>(smem_raw), reinterpret_cast<int *>(smem_raw) + G.ncell};
+    int *words = reinterpret_cast<int *>(smem_raw);
+    int *carry = p.carry + (size_t)blockIdx.x * p.tile_cells;
     for (int c = threadIdx.x; c < G.ncell; c += blockDim.x) {
-        tile.lo[c] = 0u;
-        tile.hi[c] = 0;
+        words[c] = 0;
+        carry[c] = 0;
     }
     __syncthreads();
     const double Bnd = *p.bound;
     const int Eg = global_exponent(Bnd);
-    // Tile unit 2^-Et with Et = Eg - 10 (still below 2^-50 B); kept inside the float range for
+    // Tile unit 2^-Et with Et = Eg - kTileBits (2^-47 B or finer); kept inside the float range for
     // tiny inputs (a coarser unit there).
-    const int Et = min(Eg - 10, 120);
+    const int Et = min(Eg - kTileBits, 120);
     const int shift = Eg - Et;
+    const SplitTile tile{words, carry};
     const float sc = (float)ldexp(1.0, Et);
     const float tau = (float)*p.tau;
     long long first, nthr;
     pair_schedule(p, first, nthr);
     if (p.nslab > 1) {
-        float *buf = reinterpret_cast<float *>(smem_raw + (size_t)p.rows_per_slab * G.plane * 8) +
+        float *buf = reinterpret_cast<float *>(smem_raw + (size_t)p.rows_per_slab * G.plane * 4) +
                      (threadIdx.x >> 5) * 32 * (D + 1);
-        spread_pairs_queued<float, D, W>(p, first, nthr, sc, tau, tile, G.row_lo, G.nrows, G.plane, buf);
+        spread_pairs_queued<float, D, W, SplitTile, ANG>(p, first, nthr, sc, tau, tile, G.row_lo, G.nrows, G.plane,
+                                                          buf);
     } else {
         for (long long pr = first; pr < p.npairs; pr += nthr) {
             PairData<float, D> P;
-            if (!load_pair<float, D>(p, pr, P)) continue;
+            if (!load_pair<float, D, ANG>(p, pr, P)) continue;
             if (tau > 0.0f && pair_bound<float, D>(p, P) < tau) continue;
             P.base *= P.mult;
-            spread_pair<float, D, W>(p, P, sc, tile, G.row_lo, G.nrows, G.plane);
+            spread_pair<float, D, W, SplitTile, ANG>(p, P, sc, tile, G.row_lo, G.nrows, G.plane);
         }
     }
     __syncthreads();
-    unsigned long long *gdst = p.grid + (size_t)G.row_lo * G.plane;
     for (int c = threadIdx.x; c < G.ncell; c += blockDim.x) {
-        const long long v = (long long)(((unsigned long long)(unsigned)tile.hi[c] << 32) | tile.lo[c]);
-        // |v 2^shift| <= B 2^Eg <= 2^61, so a non-zero v never comes with shift > 61
-        if (v && shift <= 62) atomicAdd(gdst + c, (unsigned long long)(v * (1ll << shift)));
+        const long long v = tile.value(c);
+        // |v 2^shift| <= B 2^Eg <= 2^61
+        if (v)
+            atomicAdd(p.grid + tile_to_grid_cell(c, D, p.nf, p.ncol, p.cpad, p.n, G.row_lo),
+                      (unsigned long long)(v * (1ll << shift)));
     }
 }
 
-template <int D, int W>
+template <int D, int W, bool ANG>
 __global__ void __launch_bounds__(kMaxThreadsF64) k_spread_f64(const __grid_constant__ SpreadArgs p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -616,68 +654,59 @@ __global__ void __launch_bounds__(kMaxThreadsF64) k_spread_f64(const __grid_cons
     if (p.nslab > 1) {
         double *buf = reinterpret_cast<double *>(smem_raw + (size_t)p.rows_per_slab * G.plane * 8) +
                       (threadIdx.x >> 5) * 32 * (D + 1);
-        spread_pairs_queued<double, D, W>(p, first, nthr, 1.0, tau, tile, G.row_lo, G.nrows, G.plane, buf);
+        spread_pairs_queued<double, D, W, DoubleTile, ANG>(p, first, nthr, 1.0, tau, tile, G.row_lo, G.nrows,
+                                                            G.plane, buf);
     } else {
         for (long long pr = first; pr < p.npairs; pr += nthr) {
             PairData<double, D> P;
-            if (!load_pair<double, D>(p, pr, P)) continue;
+            if (!load_pair<double, D, ANG>(p, pr, P)) continue;
             if (tau > 0.0 && pair_bound<double, D>(p, P) < tau) continue;
             P.base *= P.mult;
-            spread_pair<double, D, W>(p, P, 1.0, tile, G.row_lo, G.nrows, G.plane);
+            spread_pair<double, D, W, DoubleTile, ANG>(p, P, 1.0, tile, G.row_lo, G.nrows, G.plane);
         }
     }
     __syncthreads();
     // block partial sums -> the grid's fixed-point unit (|v| 2^Eg <= 2^61); the rounding of a
     // partial sum is 2^-61 B at most
-    unsigned long long *gdst = p.grid + (size_t)G.row_lo * G.plane;
     const double sc = ldexp(1.0, Eg);
     for (int c = threadIdx.x; c < G.ncell; c += blockDim.x) {
         const long long v = __double2ll_rn(tile.v[c] * sc);
-        if (v) atomicAdd(gdst + c, (unsigned long long)v);
+        if (v)
+            atomicAdd(p.grid + tile_to_grid_cell(c, D, p.nf, p.ncol, p.cpad, p.n, G.row_lo), (unsigned long long)v);
     }
 }
 
-template <int D, int W>
+template <int D, int W, bool ANG>
 cudaError_t launch_f32(const SpreadArgs &a, int blocks, int threads, size_t smem, cudaStream_t s)
 {
-    auto kern = k_spread_f32<D, W>;
+    auto kern = k_spread_f32<D, W, ANG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<blocks, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int D, int W>
+template <int D, int W, bool ANG>
 cudaError_t launch_f64(const SpreadArgs &a, int blocks, int threads, size_t smem, cudaStream_t s)
 {
-    auto kern = k_spread_f64<D, W>;
+    auto kern = k_spread_f64<D, W, ANG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<blocks, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-// Compile-time dispatch on the kernel width w in [W, WMAX].
-template <bool F32, int D, int W, int WMAX>
+// Compile-time dispatch on the kernel width w in [W, WMAX].  ANG: the angular-kernel variant
+// (instantiated in its own translation units).
+template <bool F32, int D, int W, int WMAX, bool ANG>
 struct WidthDispatch {
     static cudaError_t run(const SpreadArgs &a, int w, int blocks, int threads, size_t smem, cudaStream_t s)
     {
         if (w == W) {
-            if constexpr (F32) return launch_f32<D, W>(a, blocks, threads, smem, s);
-            else return launch_f64<D, W>(a, blocks, threads, smem, s);
+            if constexpr (F32) return launch_f32<D, W, ANG>(a, blocks, threads, smem, s);
+            else return launch_f64<D, W, ANG>(a, blocks, threads, smem, s);
         }
-        return WidthDispatch<F32, D, W + 1, WMAX>::run(a, w, blocks, threads, smem, s);
-    }
-};
-
-template <bool F32, int D, int WMAX>
-struct WidthDispatch<F32, D, WMAX, WMAX> {
-    static cudaError_t run(const SpreadArgs &a, int w, int blocks, int threads, size_t smem, cudaStream_t s)
-    {
-        if (w == WMAX) {
-            if constexpr (F32) return launch_f32<D, WMAX>(a, blocks, threads, smem, s);
-            else return launch_f64<D, WMAX>(a, blocks, threads, smem, s);
-        }
+        if constexpr (W < WMAX) return WidthDispatch<F32, D, W + 1, WMAX, ANG>::run(a, w, blocks, threads, smem, s);
         return cudaErrorInvalidValue;
     }
 };

@@ -98,9 +98,30 @@ constexpr int kLossThreads = 128;
 // strengths sum_{j,m} |q_ijm| (times Bconst, which Bw carries).  PT is the arithmetic of the
 // pair terms: FP64, or FP32 for the FP32 path, where 64-term partial sums are FP32 and
 // everything above them FP64.
+// b(cos theta) summed over the sphere set for the pair direction dvec = v_i - v_j (|dvec| = g):
+// (1/Wsig) sum_m w_m b(dvec . sigma_m / g), cos theta = 0 when g = 0 (Eq. collision_form).
+template <typename PT>
+__device__ __forceinline__ PT angular_mean(const Angular &ang, const PT *dvec, PT g, int d, int M,
+                                           const PT *__restrict__ sig, const PT *__restrict__ wsig, PT inv_wsig)
+{
+    const PT ginv = g > PT(0) ? PT(1) / g : PT(0);
+    PT acc = PT(0);
+    for (int m = 0; m < M; ++m) {
+        PT c = PT(0);
+        for (int l = 0; l < d; ++l) c += dvec[l] * sig[m * d + l];
+        c *= ginv;
+        PT b = PT(ang.c[ang.n - 1]);
+        for (int t = ang.n - 2; t >= 0; --t) b = b * c + PT(ang.c[t]);
+        acc += wsig[m] * b;
+    }
+    return acc * inv_wsig;
+}
+
 template <typename PT>
 __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict__ a,
-                                                        const PT *__restrict__ vnode, int N, int d,
+                                                        const PT *__restrict__ vnode, int N, int d, int M,
+                                                        const PT *__restrict__ sig, const PT *__restrict__ wsig,
+                                                        const Angular ang, double angmax, double Wsig,
                                                         double gamma, int fast_gamma, double Bw,
                                                         const double *__restrict__ inv_mu2, double S, int r,
                                                         double *__restrict__ h, double *__restrict__ ub,
@@ -123,19 +144,20 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict_
     PT vi[3];
     for (int l = 0; l < 3; ++l) vi[l] = (l < d) ? vnode[idx[l]] : PT(0);
     const PT Sp = PT(S), invS = PT(1) / Sp, gam = PT(gamma);
-    const double ai_w = fabs(a[i]) * Bw;  // pair bound = ai_w * |a_j| B_ij prod mu^-2
+    const double ai_w = fabs(a[i]) * Bw * angmax;  // pair bound = ai_w * |a_j| B_ij prod mu^-2
+    const PT inv_wsig = PT(1.0 / Wsig);
     double acc = 0.0, bnd = 0.0;
     for (int j0 = threadIdx.x * 64; j0 < nnode; j0 += blockDim.x * 64) {
         PT lp = PT(0), bp = PT(0);
         const int j1 = min(j0 + 64, nnode);
         for (int j = j0; j < j1; ++j) {
             int t = j;
-            PT g2 = PT(0), vj[3] = {PT(0), PT(0), PT(0)};
+            PT g2 = PT(0), vj[3] = {PT(0), PT(0), PT(0)}, dv[3] = {PT(0), PT(0), PT(0)};
             for (int l = d - 1; l >= 0; --l) {
                 vj[l] = vnode[t % N];
                 t /= N;
-                const PT dl = vi[l] - vj[l];
-                g2 += dl * dl;
+                dv[l] = vi[l] - vj[l];
+                g2 += dv[l] * dv[l];
             }
             const PT g = sqrt(g2);
             PT B;
@@ -146,7 +168,11 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict_
             default: B = (g2 > PT(0)) ? pow(g, gam) : PT(0); break;
             }
             const PT aj = PT(a[j]);
-            lp += aj * B;
+            // explicit FMA: the batched plans' loss sums the same terms the same way
+            if (ang.n)
+                lp = fma(aj * B, angular_mean<PT>(ang, dv, g, d, M, sig, wsig, inv_wsig), lp);
+            else
+                lp = fma(aj, B, lp);
             if (aj != PT(0) && B != PT(0)) {
                 PT mu = PT(1);
                 for (int l = 0; l < d; ++l) {
@@ -167,7 +193,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict_
         double sc = 1.0;
         for (int l = 0; l < d; ++l) sc *= inv_mu2[idx[l]];
         h[i] = a[i] * Bw * tot * sc;
-        ub[i] = fabs(a[i]) * Bw * tb;
+        ub[i] = fabs(a[i]) * Bw * angmax * tb;
     }
     if (hist) {
         __syncthreads();
@@ -312,13 +338,15 @@ constexpr int kWeakThreads = 256;
 // Discrete weak form of the collision operator (Eq. weak with the quadrature of Section 4):
 //   out[2t]   = sum_{i,j,m} qbar [phi_t(v') - phi_t(v_i)],
 //   out[2t+1] = sum_{i,j,m} qbar (|phi_t(v')| + |phi_t(v_i)|),
-// qbar = a_i a_j w_m Bconst |v_i - v_j|^gamma, for phi_t in {1, v_1, .., v_d, |v|^2} (t = 0..d+1).
+// qbar = a_i a_j w_m Bconst |v_i - v_j|^gamma b(cos theta_ijm), for phi_t in {1, v_1, .., v_d, |v|^2}
+// (t = 0..d+1), cos theta_ijm = (v_i - v_j) . sigma_m / |v_i - v_j| (0 when i = j).
 // One thread per node pair, FP64 throughout; block sums are added to out with atomics.
 __global__ void __launch_bounds__(kWeakThreads) k_weak_moments(const double *__restrict__ a,
                                                                const double *__restrict__ vnode, int N, int d,
                                                                int M, const double *__restrict__ sig,
-                                                               const double *__restrict__ wsig, double gamma,
-                                                               int fast_gamma, double Bconst, double *__restrict__ out)
+                                                               const double *__restrict__ wsig, const Angular ang,
+                                                               double gamma, int fast_gamma, double Bconst,
+                                                               double *__restrict__ out)
 {
     const int nnode = (d == 2) ? N * N : N * N * N;
     const long long npairs = (long long)nnode * nnode;
@@ -348,8 +376,17 @@ __global__ void __launch_bounds__(kWeakThreads) k_weak_moments(const double *__r
         }
         double vi2 = 0.0;
         for (int l = 0; l < d; ++l) vi2 += vi[l] * vi[l];
+        const double ginv = g > 0.0 ? 1.0 / g : 0.0;
         for (int m = 0; m < M; ++m) {
-            const double q = aij * B * wsig[m];
+            double bang = 1.0;
+            if (ang.n) {
+                double c = 0.0;
+                for (int l = 0; l < d; ++l) c += (vi[l] - vj[l]) * sig[m * d + l];
+                c *= ginv;
+                bang = ang.c[ang.n - 1];
+                for (int t = ang.n - 2; t >= 0; --t) bang = bang * c + ang.c[t];
+            }
+            const double q = aij * B * wsig[m] * bang;
             double vp2 = 0.0;
             for (int l = 0; l < d; ++l) {
                 const double vp = 0.5 * (vi[l] + vj[l]) + 0.5 * g * sig[m * d + l];
@@ -420,17 +457,19 @@ cudaError_t launch_recon_last(const double *in, Dims3 in_dims, const double *A, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_loss(const double *a, const double *vnode, const float *vnode32, int N, int d, double gamma,
+cudaError_t launch_loss(const double *a, const double *vnode, const float *vnode32, int N, int d, int M,
+                        const double *sig, const double *wsig, const float *sig32, const float *wsig32,
+                        const Angular &ang, double angmax, double Wsig, double gamma,
                         int fast_gamma, double Bw, const double *inv_mu2, double S, int r, double *h,
                         double *ub, unsigned long long *hist, cudaStream_t s)
 {
     const int nnode = (d == 2) ? N * N : N * N * N;
     if (vnode32)
-        k_loss<float><<<nnode, kLossThreads, 0, s>>>(a, vnode32, N, d, gamma, fast_gamma, Bw, inv_mu2, S, r, h, ub,
-                                                     hist);
+        k_loss<float><<<nnode, kLossThreads, 0, s>>>(a, vnode32, N, d, M, sig32, wsig32, ang, angmax, Wsig, gamma,
+                                                     fast_gamma, Bw, inv_mu2, S, r, h, ub, hist);
     else
-        k_loss<double><<<nnode, kLossThreads, 0, s>>>(a, vnode, N, d, gamma, fast_gamma, Bw, inv_mu2, S, r, h, ub,
-                                                      hist);
+        k_loss<double><<<nnode, kLossThreads, 0, s>>>(a, vnode, N, d, M, sig, wsig, ang, angmax, Wsig, gamma,
+                                                      fast_gamma, Bw, inv_mu2, S, r, h, ub, hist);
     return cudaGetLastError();
 }
 
@@ -475,10 +514,11 @@ cudaError_t launch_rk4_update(double *f, const double *k1, const double *k2, con
 }
 
 cudaError_t launch_weak_moments(const double *a, const double *vnode, int N, int d, int M, const double *sig,
-                                const double *wsig, double gamma, int fast_gamma, double Bconst, double *out,
-                                cudaStream_t s)
+                                const double *wsig, const Angular &ang, double gamma, int fast_gamma, double Bconst,
+                                double *out, cudaStream_t s)
 {
-    k_weak_moments<<<4 * 152, kWeakThreads, 0, s>>>(a, vnode, N, d, M, sig, wsig, gamma, fast_gamma, Bconst, out);
+    k_weak_moments<<<4 * 152, kWeakThreads, 0, s>>>(a, vnode, N, d, M, sig, wsig, ang, gamma, fast_gamma, Bconst,
+                                                    out);
     return cudaGetLastError();
 }
 

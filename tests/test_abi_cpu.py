@@ -71,6 +71,21 @@ def test_extended_option_validation(L):
     o = _lib.Opts(d=2, N=8, M=8, S=2.0, kernel_gamma=0.0, tol=1e-6, map_log=3)
     assert not L.pg_boltz_plan_ex(ctypes.byref(o))
     assert "map_log" in _lib.last_error()
+    o = _lib.Opts(d=2, N=8, M=8, S=2.0, kernel_gamma=0.0, tol=1e-6, angular_terms=9)
+    assert not L.pg_boltz_plan_ex(ctypes.byref(o))
+    assert "angular_terms" in _lib.last_error()
+    o = _lib.Opts(d=2, N=8, M=8, S=2.0, kernel_gamma=0.0, tol=1e-6, angular_terms=2)  # NULL coefficients
+    assert not L.pg_boltz_plan_ex(ctypes.byref(o))
+    assert "angular_coef" in _lib.last_error()
+    bad = (ctypes.c_double * 2)(1.0, float("nan"))
+    o = _lib.Opts(d=2, N=8, M=8, S=2.0, kernel_gamma=0.0, tol=1e-6, angular_terms=2,
+                  angular_coef=ctypes.cast(bad, ctypes.POINTER(ctypes.c_double)))
+    assert not L.pg_boltz_plan_ex(ctypes.byref(o))
+    assert "not finite" in _lib.last_error()
+    n, m, sv, gv = (ctypes.c_int * 1)(8), (ctypes.c_int * 1)(8), (ctypes.c_double * 1)(2.0), (ctypes.c_double * 1)(0.0)
+    o = _lib.Opts(d=2, tol=1e-6, angular_terms=1, angular_coef=ctypes.cast(sv, ctypes.POINTER(ctypes.c_double)))
+    assert not L.pg_boltz_plan_batched_ex(ctypes.byref(o), 1, n, m, sv, gv)
+    assert "VHS" in _lib.last_error()
 
 
 @pytest.mark.parametrize("r", [0, 1])
