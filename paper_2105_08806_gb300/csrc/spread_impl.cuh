@@ -364,9 +364,13 @@ __device__ __forceinline__ void make_point(const SpreadArgs &p, const PairData<T
             z = Fn<T>::atan2_(S, vp);
             m2 = (SS + vp * vp) * invS;
         } else {
-            const T u = vp * invS;
-            z = Fn<T>::atan2_(T(1), Fn<T>::sinh_(u));
-            m2 = S * Fn<T>::cosh_(u);
+            // z = 2 atan(e^-u) and mu^-2 = S cosh u with e = e^-|u| <= 1 (one exp and one atan
+            // instead of sinh, cosh and atan2): for u < 0, 2 atan(e^|u|) = pi - 2 atan(e^-|u|)
+            const double u = vp * invS;
+            const double e = exp(-fabs(u));
+            const double at2 = 2.0 * atan(e);
+            z = u >= 0.0 ? at2 : 3.14159265358979323846 - at2;
+            m2 = 0.5 * S * (e + 1.0 / e);
         }
         q *= m2;
         x[l] = z * gs;
