@@ -26,13 +26,14 @@
 //    memory; at the end each cell's partial sum is rounded to the grid unit (relative error
 //    2^-61 B) and added to the global grid.
 //  - FP32 kernel: the private copy holds one signed 32-bit fixed-point word per cell in units of
-//    2^-Et, Et = Eg - kTileBits (SplitTile): a contribution goes to its word with one native
-//    32-bit shared atomic, and only an addition that overflows the word's signed range (seen
-//    from the returned old value) sends the wrapped 2^32 units to the cell's int64 entry of the
-//    global grid.  (Floating-point shared atomics are compare-and-swap loops and their rounding
-//    limits FP32 accuracy; 64-bit integer shared atomics are several times slower than 32-bit
-//    ones.)  At the end each block adds its words (scaled by 2^kTileBits) to the global grid.
-//    Each contribution is rounded once, to the tile unit; all later additions are exact.
+//    2^-Et, Et = Eg - kTileBits, plus per-cell carry counters in a per-block global array
+//    (SplitTile): a contribution goes to its word with one native 32-bit shared atomic, and only
+//    an addition that wraps the word's signed range (seen from the returned old value) adds +-1
+//    to the cell's carry counter (units of 2^32).  (Floating-point shared atomics are
+//    compare-and-swap loops and their rounding limits FP32 accuracy; 64-bit integer shared
+//    atomics are several times slower than 32-bit ones.)  At the end each block adds
+//    word + carry 2^32 (scaled by 2^kTileBits) to the global grid.  Each contribution is rounded
+//    once, to the tile unit; all later additions are exact.
 #pragma once
 
 #include <climits>
