@@ -301,7 +301,24 @@ __device__ __forceinline__ void cell_args(const BatchArgs &b, const CellDesc &cd
 }
 
 template <typename T>
-constexpr int max_threads_of() { return sizeof(T) == 4 ? kMaxThreadsF32 : kMaxThreadsF64; }
+constexpr int max_threads_of() { return sizeof(T) == 4 ? kBatchThreadsF32 : kMaxThreadsF64; }
+
+// Add a cell's block tile to the cell's global grid (padding columns folded onto their cells).
+template <bool F32, int D>
+__device__ __forceinline__ void batch_flush(const int *lo, const int *carry, const double *dv, int ncell, int nf,
+                                            int ncol, int cpad, int n, unsigned long long *grid, int shift, int Eg)
+{
+    for (int e = threadIdx.x; e < ncell; e += blockDim.x) {
+        const int gc = spread_detail::tile_to_grid_cell(e, D, nf, ncol, cpad, n, 0);
+        if constexpr (F32) {
+            const long long v = (long long)carry[e] * 4294967296LL + lo[e];
+            if (v) atomicAdd(grid + gc, (unsigned long long)(v * (1ll << shift)));
+        } else {
+            const long long v = __double2ll_rn(dv[e] * ldexp(1.0, Eg));
+            if (v) atomicAdd(grid + gc, (unsigned long long)v);
+        }
+    }
+}
 
 template <typename T, int D, int W>
 __global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __grid_constant__ BatchArgs b)
@@ -318,18 +335,6 @@ __global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __gr
     int *carry = F32 ? b.carry + (size_t)blockIdx.x * b.carry_stride : nullptr;
     double *dv = reinterpret_cast<double *>(smem_raw);
     // add the current cell's tile to its grid (padding columns folded onto their cells)
-    auto flush = [&]() {
-        for (int e = threadIdx.x; e < ncell; e += blockDim.x) {
-            const int gc = tile_to_grid_cell(e, D, s_cd.nf, sa.ncol, sa.cpad, s_cd.n, 0);
-            if constexpr (F32) {
-                const long long v = SplitTile{lo, carry}.value(e);
-                if (v) atomicAdd(sa.grid + gc, (unsigned long long)(v * (1ll << shift)));
-            } else {
-                const long long v = __double2ll_rn(dv[e] * ldexp(1.0, Eg));
-                if (v) atomicAdd(sa.grid + gc, (unsigned long long)v);
-            }
-        }
-    };
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(b.counter, 1);
@@ -338,7 +343,8 @@ __global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __gr
         if (item >= b.nitems) break;  // uniform over the block
         const int cell = b.item_cell[item];
         if (cell != cur) {
-            if (cur >= 0) flush();  // the previous cell's tile
+            if (cur >= 0)  // the previous cell's tile
+                batch_flush<F32, D>(lo, carry, dv, ncell, s_cd.nf, sa.ncol, sa.cpad, s_cd.n, sa.grid, shift, Eg);
             __syncthreads();
             if (threadIdx.x == 0) s_cd = b.cells[cell];
             __syncthreads();
@@ -379,7 +385,7 @@ __global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __gr
         }
         __syncthreads();
     }
-    if (cur >= 0) flush();
+    if (cur >= 0) batch_flush<F32, D>(lo, carry, dv, ncell, s_cd.nf, sa.ncol, sa.cpad, s_cd.n, sa.grid, shift, Eg);
 }
 
 // One block per cell: Q = D(grid) - E(h) along every axis (Section 4.2).
@@ -748,7 +754,7 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
         free_plan(p);
         return nullptr;
     }
-    const int max_threads = f32 ? pgb::kMaxThreadsF32 : pgb::kMaxThreadsF64;
+    const int max_threads = f32 ? pgb::kBatchThreadsF32 : pgb::kMaxThreadsF64;
     int per_sm = (int)(prop.sharedMemPerMultiprocessor / (B->spread_smem + 2048 + prop.reservedSharedMemPerBlock));
     per_sm = std::max(per_sm, 1);
     if (o.spread_blocks_per_sm > 0) per_sm = std::min(per_sm, o.spread_blocks_per_sm);
