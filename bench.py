@@ -34,6 +34,17 @@ UNIT = "Q evals/s"
 # capture summarised in profiles/k_spread_f32_2d_w6_N64_full.md; keyed by kernel and
 # configuration, to be re-taken whenever the kernel changes.
 PROFILED_TRAFFIC = {("k_spread_f32<2,6>", 64, 32, 1e-6): 210944}
+# --workload: the headline (default) and the other single-plan configurations, for measuring and
+# profiling them with the same harness; name -> (workloads.py constructor, description)
+WORKLOADS = {
+    "2d-hard-spheres": ("c2_2d_vhs", "2D hard spheres (gamma=1), N=64 (65^2 modes), M=32 circle points, S=3, algebraic map"),
+    "2d-maxwell": ("c1_2d_maxwell", "2D Maxwell molecules (gamma=0), N=16, M=8 circle points, S=2, algebraic map"),
+    "3d-bkw": ("c3_3d_bkw", "3D Maxwell molecules on the BKW datum (K=3/5), N=16, M=32 antipodal Fibonacci "
+                            "points, S=2, algebraic map"),
+    "3d-bimaxwell": ("c4_3d_bimaxwell", "3D VHS gamma=1/2 on a bi-Maxwellian (T=0.6/1.4/1.4), N=24, M=32 antipodal "
+                                        "Fibonacci points, S=3, algebraic map"),
+}
+DEFAULT_WORKLOAD = "2d-hard-spheres"
 
 
 def parse():
@@ -49,6 +60,8 @@ def parse():
     ap.add_argument("--upsampfac", type=float, default=0.0)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=2)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD,
+                    help="single-plan configuration (the batched run and the CPU baseline go with the default)")
     return ap.parse_args()
 
 
@@ -228,14 +241,17 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     build()
-    w = Wl.c2_2d_vhs()
+    default = args.workload == DEFAULT_WORKLOAD
+    w = getattr(Wl, WORKLOADS[args.workload][0])()
     d, N, M, S, gamma = w.d, w.N, w.M, w.S, w.gamma
     stream = torch.cuda.Stream(device=dev)
     plan32 = Plan(d, N, M, S, gamma, args.tol32, precision=PG_PREC_FP32, upsampfac=args.upsampfac)
-    plan64 = Plan(d, N, M, S, gamma, 1e-13, precision=PG_PREC_FP64)
+    plan64 = Plan(d, N, M, S, gamma, 1e-13, precision=PG_PREC_FP64) if args.fp64_steps > 0 else None
     for p in (plan32, plan64):
-        p.set_stream(stream)
-    info32, info64 = plan32.info(), plan64.info()
+        if p is not None:
+            p.set_stream(stream)
+    info32 = plan32.info()
+    info64 = plan64.info() if plan64 is not None else None
 
     # input: f at the projection nodes (seeded workload density), projected on the GPU
     import numpy as np
@@ -281,7 +297,9 @@ def run_ours(args):
     with ClockSampler(local, enabled=not args.no_clocks) as clk:
         ms32, st32, wall32 = timed_loop(plan32, Q, args.steps, args.warmup)
     clocks = clk.summary()
-    ms64, st64, _ = timed_loop(plan64, Q64, max(1, args.fp64_steps), 1)
+    ms64, st64 = None, None
+    if plan64 is not None:
+        ms64, st64, _ = timed_loop(plan64, Q64, args.fp64_steps, 1)
     # screened variant of the FP32 path (skips the node pairs with the smallest strength bounds)
     plan_sc = Plan(d, N, M, S, gamma, args.tol32, precision=PG_PREC_FP32, upsampfac=args.upsampfac, screen=True)
     plan_sc.set_stream(stream)
@@ -309,11 +327,11 @@ def run_ours(args):
             e2e_ms.append(a.elapsed_time(b))
 
     mean32, mean_e2e = reduce_max([statistics.mean(ms32), statistics.mean(e2e_ms)], world, dev)
-    err = float(torch.linalg.norm(Q - Q64) / torch.linalg.norm(Q64))
-    err_sc = float(torch.linalg.norm(Qsc - Q64) / torch.linalg.norm(Q64))
+    err = float(torch.linalg.norm(Q - Q64) / torch.linalg.norm(Q64)) if plan64 is not None else None
+    err_sc = float(torch.linalg.norm(Qsc - Q64) / torch.linalg.norm(Q64)) if plan64 is not None else None
     plan_sc.close()
-    batched = None if args.no_batched else run_batched(max(1, args.batched_steps), stream, dev)
-    mom = plan64.moments()
+    batched = None if (args.no_batched or not default) else run_batched(max(1, args.batched_steps), stream, dev)
+    mom = plan64.moments() if plan64 is not None else None
 
     # roofline of the dominant kernel (spreading): one shared-memory atomic add per
     # contribution, w^d contributions for each of the M N^d (N^d + 1)/2 points per launch
@@ -328,7 +346,7 @@ def run_ours(args):
     measured_atomic = probe_shared_atomics(stream)
     stage_names = ["reconstruct", "loss", "spread", "transform"]
     stage_mean32 = {n: statistics.mean(s[i] for s in st32) for i, n in enumerate(stage_names)}
-    stage_mean64 = {n: statistics.mean(s[i] for s in st64) for i, n in enumerate(stage_names)}
+    stage_mean64 = {n: statistics.mean(s[i] for s in st64) for i, n in enumerate(stage_names)} if st64 else None
 
     value = aggregate_throughput(mean32, world)
     res = {
@@ -343,9 +361,10 @@ def run_ours(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
-        "data": "synthetic (seeded three-Maxwellian + perturbation density, projected on the GPU)",
+        "data": ("synthetic (seeded three-Maxwellian + perturbation density, projected on the GPU)" if default
+                 else "synthetic (the workload's seeded density, projected on the GPU)"),
         "config": {
-            "workload": "2D hard spheres (gamma=1), N=64 (65^2 modes), M=32 circle points, S=3, algebraic map",
+            "workload": WORKLOADS[args.workload][1],
             "spread_precision": f"fp32 (tol {args.tol32:g}); loss, transform, deconvolution fp64",
             "upsampfac": info32["upsampfac"],
             "kernel_width": wgt, "n_grid": info32["n_grid"], "n_fold": info32["n_fold"],
@@ -356,20 +375,21 @@ def run_ours(args):
         "points_per_s": value * info32["points"],
         "points_per_s_paper_convention": value * M * (N + 2) ** (2 * d),
         "rel_err_fp32_vs_fp64_path": err,
-        "fp64_path": {"value": 1000.0 / statistics.mean(ms64), "ms_per_step": statistics.mean(ms64),
-                      "steps": len(ms64), "kernel_width": info64["kernel_width"], "stages_ms": stage_mean64},
-        "speedup_fp32_vs_fp64": statistics.mean(ms64) / mean32,
+        "fp64_path": ({"value": 1000.0 / statistics.mean(ms64), "ms_per_step": statistics.mean(ms64),
+                       "steps": len(ms64), "kernel_width": info64["kernel_width"], "stages_ms": stage_mean64}
+                      if ms64 else None),
+        "speedup_fp32_vs_fp64": statistics.mean(ms64) / mean32 if ms64 else None,
         "screened": {"value": 1000.0 / statistics.mean(ms_sc), "ms_per_step": statistics.mean(ms_sc),
                      "rel_err_vs_fp64_path": err_sc,
                      "note": "screen=1: node pairs whose summed strength bound is below 0.05 tol B are skipped"},
         "batched": batched,
         "stages_ms": stage_mean32,
-        "conservation_fp64": {"mass_rel": abs(mom["mass"]) / abs(mom["mass_gain"]),
-                              "energy_rel": abs(mom["energy"]) / abs(mom["energy_gain"])},
+        "conservation_fp64": ({"mass_rel": abs(mom["mass"]) / abs(mom["mass_gain"]),
+                               "energy_rel": abs(mom["energy"]) / abs(mom["energy_gain"])} if mom else None),
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_rmw / 1e9,
                      "unit": "G shared-memory RMW/s", "frac": achieved / peak_rmw,
                      "traffic": PROFILED_TRAFFIC.get((f"k_spread_f32<{d},{wgt}>", N, M, args.tol32)),
-                     "kernel": "k_spread<float,2,%d>" % wgt,
+                     "kernel": "k_spread<float,%d,%d>" % (d, wgt),
                      "peak_basis": f"{sm_count} SMs x 32 shared-memory lanes/clk x 2070 MHz (derived)",
                      "measured_atomic_peak": measured_atomic / 1e9,
                      "frac_of_measured_atomic_peak": achieved / measured_atomic,
@@ -381,9 +401,10 @@ def run_ours(args):
         "wall_s_timed_region": wall32,
     }
     plan32.close()
-    plan64.close()
+    if plan64 is not None:
+        plan64.close()
     if rank == 0:
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and default:
             res["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(res))
     if world > 1:

@@ -44,3 +44,16 @@ def test_single_rank_is_identity():
     import bench
     assert bench.reduce_max([1.5, 2.5], 1) == [1.5, 2.5]
     assert bench.aggregate_throughput(20.0, 1) == pytest.approx(50.0)
+
+
+def test_bench_workloads_name_the_seeded_configurations():
+    """Every --workload of bench.py builds one of the seeded workloads, with its N, M, S, gamma."""
+    import bench
+    from paper_2105_08806_gb300 import workloads as W
+    expect = {"2d-hard-spheres": (2, 64, 32), "2d-maxwell": (2, 16, 8), "3d-bkw": (3, 16, 32),
+              "3d-bimaxwell": (3, 24, 32)}
+    assert bench.DEFAULT_WORKLOAD == "2d-hard-spheres" and set(bench.WORKLOADS) == set(expect)
+    for name, (ctor, desc) in bench.WORKLOADS.items():
+        w = getattr(W, ctor)()
+        assert (w.d, w.N, w.M) == expect[name], name
+        assert f"N={w.N}" in desc and f"M={w.M}" in desc
