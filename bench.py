@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--upsampfac", type=float, default=0.0)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=2)
+    ap.add_argument("--batched-cells", type=int, default=0,
+                    help="run the batched workload on its first K cells only (0: all 4096; for profiling)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD,
                     help="single-plan configuration (the batched run and the CPU baseline go with the default)")
     return ap.parse_args()
@@ -174,7 +176,7 @@ def cpu_baseline(workload, budget_s=12.0):
 
 
 # ------------------------------------------------------------------ batched
-def run_batched(steps, stream, dev):
+def run_batched(steps, stream, dev, ncells=0):
     """The 4096-cell batched 2D workload: N in {16,24,32}, M in {8,16,32}, gamma in {0,1}, S=3,
     FP32 spreading (tol 1e-6), one graph-replayed pg_boltz_collide_batched per step."""
     import numpy as np
@@ -184,6 +186,8 @@ def run_batched(steps, stream, dev):
     from paper_2105_08806_gb300 import workloads as Wl
 
     cells = Wl.c5_batched_2d()
+    if ncells > 0:
+        cells = cells[:ncells]
     d = 2
     fts, plans = [], {}
     for w in cells:  # each cell's density projected on the GPU with a plan of its N
@@ -223,7 +227,8 @@ def run_batched(steps, stream, dev):
             "points_per_s": info["points"] * 1000.0 / t, "points_per_batch": info["points"],
             "spread_blocks": info["spread_blocks"], "spread_threads": info["spread_threads"],
             "steps": steps, "launches_per_call": info["launches_per_collide"],
-            "workload": "4096 2D cells, N in {16,24,32}, M in {8,16,32}, gamma in {0,1}, S=3, FP32 tol 1e-6, CUDA graph"}
+            "workload": f"{len(cells)} 2D cells, N in {{16,24,32}}, M in {{8,16,32}}, gamma in {{0,1}}, S=3, "
+                        "FP32 tol 1e-6, CUDA graph"}
 
 
 # ------------------------------------------------------------------ our arm
@@ -330,7 +335,7 @@ def run_ours(args):
     err = float(torch.linalg.norm(Q - Q64) / torch.linalg.norm(Q64)) if plan64 is not None else None
     err_sc = float(torch.linalg.norm(Qsc - Q64) / torch.linalg.norm(Q64)) if plan64 is not None else None
     plan_sc.close()
-    batched = None if (args.no_batched or not default) else run_batched(max(1, args.batched_steps), stream, dev)
+    batched = None if (args.no_batched or not default) else run_batched(max(1, args.batched_steps), stream, dev, args.batched_cells)
     mom = plan64.moments() if plan64 is not None else None
 
     # roofline of the dominant kernel (spreading): one shared-memory atomic add per
