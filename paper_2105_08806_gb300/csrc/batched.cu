@@ -330,7 +330,10 @@ __global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __gr
     constexpr bool F32 = (sizeof(T) == 4);
     int cur = -1, ncell = 0, plane = 0, Eg = 0, shift = 0;
     T sc = T(0), tau = T(0);
-    SpreadArgs sa;
+    // the current cell's spreading arguments live in shared memory: kept in registers they cost
+    // 30-odd registers per thread (fewer resident warps, or spills under a 1024-thread bound)
+    __shared__ SpreadArgs s_sa;
+    SpreadArgs &sa = s_sa;
     int *lo = reinterpret_cast<int *>(smem_raw);
     int *carry = F32 ? b.carry + (size_t)blockIdx.x * b.carry_stride : nullptr;
     double *dv = reinterpret_cast<double *>(smem_raw);
@@ -349,7 +352,8 @@ __global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __gr
             if (threadIdx.x == 0) s_cd = b.cells[cell];
             __syncthreads();
             cur = cell;
-            cell_args(b, s_cd, F32, sa);
+            if (threadIdx.x == 0) cell_args(b, s_cd, F32, sa);
+            __syncthreads();
             plane = (D == 3) ? s_cd.nf * sa.ncol : sa.ncol;
             ncell = plane * s_cd.nf;
             const double Bc = b.Bcell[cell];

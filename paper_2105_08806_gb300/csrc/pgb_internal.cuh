@@ -99,9 +99,8 @@ constexpr int kMinWidth = 2;
 // Largest spreading block for each type (the kernels' launch bounds).
 constexpr int kMaxThreadsF32 = 1024;
 constexpr int kMaxThreadsF64 = 256;
-// Largest block of the batched FP32 spreading kernel: it keeps the current cell's spreading
-// arguments in registers, which a 1024-thread bound (64 registers) would spill.
-constexpr int kBatchThreadsF32 = 256;
+// Largest block of the batched FP32 spreading kernel.
+constexpr int kBatchThreadsF32 = 1024;
 
 // Three-axis shape of a C-order array; 2D arrays use e0 = 1.
 struct Dims3 {
