@@ -210,6 +210,8 @@ def run_batched(steps, stream, dev, ncells=0):
     bp = BatchedPlan(d, [w.N for w in cells], [w.M for w in cells], [w.S for w in cells],
                      [w.gamma for w in cells], 1e-6, precision=PG_PREC_FP32)
     bp.set_stream(stream)
+    # launch shape of the persistent spreading kernel picked by the library's autotuner (untimed)
+    tuned = bp.autotune(f, Q, trials=1)
     info = bp.info()
     bp.collide(f, Q)  # capture + first replay
     stream.synchronize()
@@ -226,6 +228,7 @@ def run_batched(steps, stream, dev, ncells=0):
     return {"cells": len(cells), "ms_per_batch": t, "cell_evals_per_s": len(cells) * 1000.0 / t,
             "points_per_s": info["points"] * 1000.0 / t, "points_per_batch": info["points"],
             "spread_blocks": info["spread_blocks"], "spread_threads": info["spread_threads"],
+            "autotuned": {"threads": tuned[0], "blocks": tuned[1], "ms": tuned[2]},
             "steps": steps, "launches_per_call": info["launches_per_collide"],
             "workload": f"{len(cells)} 2D cells, N in {{16,24,32}}, M in {{8,16,32}}, gamma in {{0,1}}, S=3, "
                         "FP32 tol 1e-6, CUDA graph"}

@@ -26,7 +26,7 @@ EXPORTS = (
     "pg_boltz_stage_times", "pg_boltz_project_noalloc", "pg_boltz_probe_shared_atomics",
     "pg_boltz_plan_batched", "pg_boltz_plan_batched_ex", "pg_boltz_collide_batched", "pg_boltz_batched_offsets",
     "pg_boltz_batched_use_graph", "pg_boltz_rk4", "pg_boltz_conservation", "pg_boltz_evaluate",
-    "pg_boltz_adaptive_scale",
+    "pg_boltz_adaptive_scale", "pg_boltz_batched_autotune",
 )
 
 
@@ -101,6 +101,7 @@ def lib():
     L.pg_boltz_batched_offsets.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.pg_boltz_batched_offsets.restype = ctypes.c_int
     L.pg_boltz_batched_use_graph.argtypes = [vp, ctypes.c_int]
+    L.pg_boltz_batched_autotune.argtypes = [vp, vp, vp, ctypes.c_int, ip, ip, dp]
     L.pg_boltz_batched_use_graph.restype = ctypes.c_int
     L.pg_boltz_conservation.argtypes = [vp, vp, dp]
     L.pg_boltz_conservation.restype = ctypes.c_int
@@ -276,6 +277,13 @@ class BatchedPlan(Plan):
 
     def collide(self, f, Q):
         _check(lib().pg_boltz_collide_batched(self._h, ctypes.c_void_p(_ptr(f)), ctypes.c_void_p(_ptr(Q))))
+
+    def autotune(self, f, Q, trials=2):
+        """Time the spreading launch shapes on (f, Q) and keep the fastest; returns (threads, blocks, ms)."""
+        thr, blk, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+        _check(lib().pg_boltz_batched_autotune(self._h, ctypes.c_void_p(_ptr(f)), ctypes.c_void_p(_ptr(Q)), int(trials),
+                                               ctypes.byref(thr), ctypes.byref(blk), ctypes.byref(ms)))
+        return thr.value, blk.value, ms.value
 
     def use_graph(self, enable: bool):
         _check(lib().pg_boltz_batched_use_graph(self._h, int(bool(enable))))

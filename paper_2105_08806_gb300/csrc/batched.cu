@@ -459,6 +459,11 @@ struct BatchDispatch {
         }
         return BatchDispatch<T, D, W + 1, WMAX>::launch(w, b, blocks, threads, smem, s);
     }
+    static cudaError_t occupancy(int w, int threads, size_t smem, int *nblocks)
+    {
+        if (w == W) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nblocks, k_batch_spread<T, D, W>, threads, smem);
+        return BatchDispatch<T, D, W + 1, WMAX>::occupancy(w, threads, smem, nblocks);
+    }
 };
 template <typename T, int D, int WMAX>
 struct BatchDispatch<T, D, WMAX, WMAX> {
@@ -472,6 +477,11 @@ struct BatchDispatch<T, D, WMAX, WMAX> {
         k_batch_spread<T, D, WMAX><<<blocks, threads, smem, s>>>(b);
         return cudaGetLastError();
     }
+    static cudaError_t occupancy(int w, int threads, size_t smem, int *nblocks)
+    {
+        if (w != WMAX) return cudaErrorInvalidValue;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nblocks, k_batch_spread<T, D, WMAX>, threads, smem);
+    }
 };
 
 // The batched spreading kernels cover the widths the FP32 path uses (w <= 10) in FP32 and
@@ -482,6 +492,15 @@ cudaError_t batch_spread_attr(bool f32, int d, int w, size_t smem)
                            : BatchDispatch<float, 3, kMinWidth, kMaxWidthF32>::attr(w, smem);
     return d == 2 ? BatchDispatch<double, 2, kMinWidth, kMaxWidthF64>::attr(w, smem)
                   : BatchDispatch<double, 3, kMinWidth, kMaxWidthF64>::attr(w, smem);
+}
+
+// Resident blocks per SM of the batched spreading kernel for a launch shape.
+cudaError_t batch_spread_occupancy(bool f32, int d, int w, int threads, size_t smem, int *nblocks)
+{
+    if (f32) return d == 2 ? BatchDispatch<float, 2, kMinWidth, kMaxWidthF32>::occupancy(w, threads, smem, nblocks)
+                           : BatchDispatch<float, 3, kMinWidth, kMaxWidthF32>::occupancy(w, threads, smem, nblocks);
+    return d == 2 ? BatchDispatch<double, 2, kMinWidth, kMaxWidthF64>::occupancy(w, threads, smem, nblocks)
+                  : BatchDispatch<double, 3, kMinWidth, kMaxWidthF64>::occupancy(w, threads, smem, nblocks);
 }
 
 cudaError_t batch_spread_launch(bool f32, int d, int w, const BatchArgs &b, int blocks, int threads, size_t smem,
@@ -506,6 +525,7 @@ struct BatchState {
     int nitems = 0;
     int spread_blocks = 0, spread_threads = 0;
     size_t spread_smem = 0;
+    int carry_blocks = 0;  // blocks the FP32 carry-counter array was sized for
     pgb::BatchArgs args{};
     bool use_graph = true;
     cudaStream_t cap_stream = nullptr;
@@ -773,6 +793,7 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
     B->spread_blocks = prop.multiProcessorCount * per_sm;
     a.carry = nullptr;
     a.carry_stride = max_cells_tile;
+    B->carry_blocks = B->spread_blocks;
     if (f32 && (rc = dev_alloc(p, (void **)&a.carry, (size_t)B->spread_blocks * max_cells_tile * sizeof(int)))) {
         free_plan(p);
         return nullptr;
@@ -882,6 +903,84 @@ PG_API int pg_boltz_batched_use_graph(pg_boltz_plan_t *p, int enable)
 {
     if (!p || !p->batch) return set_error(PG_ERR_ARG, "not a batched plan");
     p->batch->use_graph = enable != 0;
+    return PG_OK;
+}
+
+// Time a set of launch shapes of the persistent spreading kernel on the caller's data and keep the
+// fastest: threads per block in {128, 256, 512, 1024} (within the kernel's bound) and every
+// blocks-per-SM count the kernel's occupancy allows, up to the blocks the carry counters were
+// sized for.  Each shape: one launch sequence to warm up, then the best of `trials` timed ones.
+PG_API int pg_boltz_batched_autotune(pg_boltz_plan_t *p, const double *f_dev, double *Q_dev, int trials,
+                                     int *threads_out, int *blocks_out, double *ms_out)
+{
+    if (!p) return set_error(PG_ERR_ARG, "plan is NULL");
+    if (!p->batch) return set_error(PG_ERR_STATE, "pg_boltz_batched_autotune needs a batched plan");
+    if (!f_dev || !Q_dev) return set_error(PG_ERR_ARG, "f or Q is NULL");
+    if (trials < 1 || trials > 100) return set_error(PG_ERR_ARG, "trials must be in [1, 100]");
+    BatchState &B = *p->batch;
+    const long long modes = B.offsets.back();
+    const char *fb = reinterpret_cast<const char *>(f_dev);
+    const char *qb = reinterpret_cast<const char *>(Q_dev);
+    if (fb < qb + modes * 8 && qb < fb + modes * 8) return set_error(PG_ERR_ARG, "f and Q overlap");
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return set_error(PG_ERR_CUDA, "cannot select the plan's device");
+    cudaDeviceProp prop;
+    int rc = cuda_check(cudaGetDeviceProperties(&prop, p->device), "cudaGetDeviceProperties");
+    if (rc) return rc;
+    const bool f32 = (B.prec == PG_PREC_FP32);
+    const int max_threads = f32 ? pgb::kBatchThreadsF32 : pgb::kMaxThreadsF64;
+    const int best0_threads = B.spread_threads, best0_blocks = B.spread_blocks;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((rc = cuda_check(cudaEventCreate(&e0), "event")) || (rc = cuda_check(cudaEventCreate(&e1), "event"))) {
+        if (e0) cudaEventDestroy(e0);
+        return rc;
+    }
+    int best_threads = best0_threads, best_blocks = best0_blocks;
+    double best_ms = 1e300;
+    for (int threads = 128; threads <= max_threads && rc == PG_OK; threads *= 2) {
+        int occ = 0;
+        if (pgb::batch_spread_occupancy(f32, B.d, B.w, threads, B.spread_smem, &occ) != cudaSuccess || occ < 1) continue;
+        for (int per_sm = 1; per_sm <= occ && rc == PG_OK; ++per_sm) {
+            const int blocks = prop.multiProcessorCount * per_sm;
+            if (f32 && blocks > B.carry_blocks) break;  // no carry counters for more blocks
+            B.spread_threads = threads;
+            B.spread_blocks = blocks;
+            double ms_best = 1e300;
+            for (int t = 0; t <= trials && rc == PG_OK; ++t) {
+                if ((rc = cuda_check(cudaEventRecord(e0, p->stream), "event record"))) break;
+                if ((rc = enqueue_batch(p, p->stream, f_dev, Q_dev))) break;
+                if ((rc = cuda_check(cudaEventRecord(e1, p->stream), "event record"))) break;
+                if ((rc = cuda_check(cudaEventSynchronize(e1), "event sync"))) break;
+                float ms = 0.0f;
+                if ((rc = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "elapsed"))) break;
+                if (t > 0) ms_best = std::min(ms_best, (double)ms);  // t = 0 warms up
+            }
+            if (rc == PG_OK && ms_best < best_ms) {
+                best_ms = ms_best;
+                best_threads = threads;
+                best_blocks = blocks;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    B.spread_threads = (rc == PG_OK) ? best_threads : best0_threads;
+    B.spread_blocks = (rc == PG_OK) ? best_blocks : best0_blocks;
+    // the captured graph holds the old launch shape: capture again on the next call
+    if (B.exec) {
+        cudaGraphExecDestroy(B.exec);
+        B.exec = nullptr;
+    }
+    if (B.graph) {
+        cudaGraphDestroy(B.graph);
+        B.graph = nullptr;
+    }
+    if (rc) return rc;
+    p->info.spread_threads = B.spread_threads;
+    p->info.spread_blocks = B.spread_blocks;
+    if (threads_out) *threads_out = B.spread_threads;
+    if (blocks_out) *blocks_out = B.spread_blocks;
+    if (ms_out) *ms_out = best_ms;
     return PG_OK;
 }
 

@@ -147,3 +147,28 @@ def test_batched_screened_matches_oracle():
     for c in range(len(Ns)):
         ref = O.collide(fts[c], d, int(Ns[c]), int(Ms[c]), float(Ss[c]), float(gs[c]))
         assert rel_l2(Qh[off[c]:off[c + 1]], ref) < 1e-10, c
+
+
+def test_autotune_keeps_results_bitwise():
+    """pg_boltz_batched_autotune times the persistent kernel's launch shapes on the caller's data
+    and keeps the fastest; the fixed-point sums do not depend on the shape, so the results before
+    and after tuning are identical, and the graph captured afterwards uses the new shape."""
+    import torch
+    from paper_2105_08806_gb300 import BatchedPlan
+    d = 2
+    Ns, Ms, Ss, gs, funs = _cells(d, 12, seed=41)
+    fts = [O.project(funs[c], d, int(Ns[c]), float(Ss[c]), 1).ravel() for c in range(len(Ns))]
+    with BatchedPlan(d, Ns, Ms, Ss, gs, 1e-6, precision=PG_PREC_FP32) as bp:
+        f = torch.as_tensor(np.concatenate(fts), device="cuda")
+        Q1 = torch.empty_like(f)
+        bp.collide(f, Q1)
+        Q2 = torch.empty_like(f)
+        thr, blocks, ms = bp.autotune(f, Q2, trials=1)
+        Q3 = torch.empty_like(f)
+        bp.collide(f, Q3)
+        torch.cuda.synchronize()
+        info = bp.info()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert thr in (128, 256, 512, 1024) and blocks % sms == 0 and ms > 0
+    assert (info["spread_threads"], info["spread_blocks"]) == (thr, blocks)
+    assert torch.equal(Q1, Q2) and torch.equal(Q1, Q3)
