@@ -224,11 +224,34 @@ def run_batched(steps, stream, dev, ncells=0):
         b.synchronize()
         ms.append(a.elapsed_time(b))
     bp.close()
+    # the same cells one pg_boltz_collide each (one plan per (N, M, S, gamma), reused across cells)
+    single = {}
+    for w in cells:
+        key = (w.N, w.M, w.S, w.gamma)
+        if key not in single:
+            single[key] = Plan(d, w.N, w.M, w.S, w.gamma, 1e-6, precision=PG_PREC_FP32)
+            single[key].set_stream(stream)
+    offs = [0]
+    for x in fts:
+        offs.append(offs[-1] + x.numel())
+    Qs = torch.empty_like(f)
+    t_single = []
+    for rep in range(2):  # the first pass warms up
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for c, w in enumerate(cells):
+            single[(w.N, w.M, w.S, w.gamma)].collide(f[offs[c]:offs[c + 1]], Qs[offs[c]:offs[c + 1]])
+        b.record(stream)
+        b.synchronize()
+        t_single.append(a.elapsed_time(b))
+    for pl in single.values():
+        pl.close()
     t = statistics.mean(ms)
     return {"cells": len(cells), "ms_per_batch": t, "cell_evals_per_s": len(cells) * 1000.0 / t,
             "points_per_s": info["points"] * 1000.0 / t, "points_per_batch": info["points"],
             "spread_blocks": info["spread_blocks"], "spread_threads": info["spread_threads"],
             "autotuned": {"threads": tuned[0], "blocks": tuned[1], "ms": tuned[2]},
+            "one_call_per_cell_ms": t_single[-1], "speedup_vs_one_call_per_cell": t_single[-1] / t,
             "steps": steps, "launches_per_call": info["launches_per_collide"],
             "workload": f"{len(cells)} 2D cells, N in {{16,24,32}}, M in {{8,16,32}}, gamma in {{0,1}}, S=3, "
                         "FP32 tol 1e-6, CUDA graph"}
