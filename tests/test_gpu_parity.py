@@ -171,6 +171,21 @@ def test_full_size_3d_bkw_against_closed_form():
     assert err < 1e-2
 
 
+@pytest.mark.slow
+def test_slabbed_2d_grid_fp32_sampled_modes():
+    """2D N = 120 in the FP32 path: the 242 x 250 tile of 4-byte words exceeds shared memory, so the
+    grid is spread in slabs through the warp point queues; sampled modes against the oracle and the
+    mode-level mass identity."""
+    d, N, M, S, gamma = 2, 120, 4, 4.0, 1.0
+    ft = O.project(_maxwell3(d, 12), d, N, S, 1).ravel()
+    modes = sample_modes(d, N, 10, seed=23)
+    gain, loss = O.collide_parts(ft, d, N, M, S, gamma, r=1, modes=modes)
+    Q, info, mom = gpu_collide(ft, d, N, M, S, gamma, 1e-6, precision=PG_PREC_FP32)
+    assert info["slabs"] >= 2
+    assert np.linalg.norm(Q[flat_index(modes, N)] - (gain - loss)) / np.linalg.norm(gain) < TOL32
+    assert abs(mom["mass"]) <= 1e-5 * abs(mom["mass_gain"])
+
+
 def test_projection_matches_oracle():
     import torch
     from paper_2105_08806_gb300 import Plan
