@@ -218,6 +218,22 @@ int pg_boltz_evaluate(pg_boltz_plan_t *plan, const double *coef_dev, long long n
  */
 int pg_boltz_adaptive_scale(int N, double L, int map_log, double *S_out);
 
+/*
+ * The FP64 spreading kernels' form of the exponential-of-semicircle kernel of the type-1 NUFFT
+ * (Eq. nufft): psi(t) = exp(beta (sqrt(1 - t^2) - 1)) for |t| < 1, t = (grid index - x) 2/w.
+ * A point at grid coordinate x touches indices s .. s+w-1, s = floor(x - w/2) + 1; with the
+ * offset y = 2 (s - x) + w - 1 in (-1, 1], tap a (t = (y + 1 + 2a - w)/w) equals, up to about
+ * exp(-beta), E_a(y^2) + y O_a(y^2) for a < ceil(w/2), and tap w-1-a equals E_a(y^2) - y O_a(y^2).
+ * For width w in [2, 16] and oversampling upsampfac in [1.5, 4] (0 -> 2) this writes beta to
+ * *beta_out, the number of terms P (w + 3 for w < 12, else w + 1) to *terms_out and
+ * ceil(w/2) * P coefficients to coef_out (host array of `capacity` doubles): block a holds the
+ * (P+1)/2 coefficients of E_a, then the P/2 of O_a, lowest power first (for odd w the middle
+ * tap's O is zero by symmetry).  Host-only.  PG_ERR_ARG for w or upsampfac out of range, NULL
+ * pointers, or capacity below ceil(w/2) * P.
+ */
+int pg_boltz_kernel_poly(int w, double upsampfac, double *coef_out, int capacity, int *terms_out,
+                         double *beta_out);
+
 /* Describe the plan (host-only). */
 int pg_boltz_info(const pg_boltz_plan_t *plan, pg_boltz_info_t *out);
 

@@ -4,6 +4,7 @@ operator Q(f, f) of arXiv 2105.08806 with the fast non-uniform-FFT algorithm (Se
 The compute path is the C ABI library libpgboltz.so (include/pg_boltz.h); this package is
 its ctypes binding (``Plan``), its nvcc build script and the seeded input distributions.
 """
-from ._lib import BatchedPlan, Plan, PGBoltzError, adaptive_scale, lib, last_error, probe_shared_atomics  # noqa: F401
+from ._lib import (BatchedPlan, Plan, PGBoltzError, adaptive_scale, kernel_poly, lib, last_error,  # noqa: F401
+                   probe_shared_atomics)
 from ._lib import PG_PREC_AUTO, PG_PREC_FP32, PG_PREC_FP64  # noqa: F401
 from ._lib import PG_SPHERE_ANTIPODAL, PG_SPHERE_AUTO, PG_SPHERE_FIBONACCI  # noqa: F401

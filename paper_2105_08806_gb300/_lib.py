@@ -26,7 +26,7 @@ EXPORTS = (
     "pg_boltz_stage_times", "pg_boltz_project_noalloc", "pg_boltz_probe_shared_atomics",
     "pg_boltz_plan_batched", "pg_boltz_plan_batched_ex", "pg_boltz_collide_batched", "pg_boltz_batched_offsets",
     "pg_boltz_batched_use_graph", "pg_boltz_rk4", "pg_boltz_conservation", "pg_boltz_evaluate",
-    "pg_boltz_adaptive_scale", "pg_boltz_batched_autotune",
+    "pg_boltz_adaptive_scale", "pg_boltz_batched_autotune", "pg_boltz_kernel_poly",
 )
 
 
@@ -85,6 +85,7 @@ def lib():
     L.pg_boltz_project.argtypes = [vp, vp, vp]
     L.pg_boltz_evaluate.argtypes = [vp, vp, ctypes.c_longlong, vp, vp]
     L.pg_boltz_adaptive_scale.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, dp]
+    L.pg_boltz_kernel_poly.argtypes = [ctypes.c_int, ctypes.c_double, dp, ctypes.c_int, ip, dp]
     L.pg_boltz_info.argtypes = [vp, ctypes.POINTER(Info)]
     L.pg_boltz_destroy.argtypes = [vp]
     L.pg_boltz_destroy.restype = None
@@ -148,6 +149,18 @@ def adaptive_scale(N: int, L: float, map_log: bool = False) -> float:
     out = ctypes.c_double(0.0)
     _check(lib().pg_boltz_adaptive_scale(int(N), float(L), int(bool(map_log)), ctypes.byref(out)))
     return out.value
+
+
+def kernel_poly(w: int, upsampfac: float = 2.0):
+    """(beta, P, coefficients) of the FP64 spreading kernels' polynomial form of the
+    exponential-of-semicircle kernel (host-only, pg_boltz_kernel_poly): ceil(w/2) blocks of P."""
+    cap = 8 * 17
+    buf = (ctypes.c_double * cap)()
+    terms = ctypes.c_int(0)
+    beta = ctypes.c_double(0.0)
+    _check(lib().pg_boltz_kernel_poly(int(w), float(upsampfac), buf, cap, ctypes.byref(terms), ctypes.byref(beta)))
+    n = (int(w) + 1) // 2 * terms.value
+    return beta.value, terms.value, list(buf[:n])
 
 
 class Plan:

@@ -74,6 +74,7 @@ struct BatchArgs {
     const float *sig32;
     const double *wsig64;
     const float *wsig32;
+    const double *kpoly;  // FP64: the kernel's polynomial coefficients (SpreadArgs::kpoly)
 };
 
 namespace {
@@ -298,6 +299,7 @@ __device__ __forceinline__ void cell_args(const BatchArgs &b, const CellDesc &cd
     sa.angmax = 1.0;
     sa.cpad = tile_col_pad(b.w);
     sa.ncol = cd.nf + 2 * sa.cpad;
+    sa.kpoly = b.kpoly;
 }
 
 template <typename T>
@@ -334,6 +336,7 @@ __global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __gr
     // 30-odd registers per thread (fewer resident warps, or spills under a 1024-thread bound)
     __shared__ SpreadArgs s_sa;
     SpreadArgs &sa = s_sa;
+    if constexpr (!F32) load_kernel_poly(b.kpoly);  // the same kernel polynomial for every cell
     int *lo = reinterpret_cast<int *>(smem_raw);
     int *carry = F32 ? b.carry + (size_t)blockIdx.x * b.carry_stride : nullptr;
     double *dv = reinterpret_cast<double *>(smem_raw);
@@ -733,10 +736,12 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
     pgb::CellDesc *d_cells = nullptr;
     int *d_items = nullptr;
     double *d_v64 = nullptr, *d_sa = nullptr, *d_im = nullptr, *d_R = nullptr, *d_E = nullptr, *d_D = nullptr,
-           *d_s64 = nullptr, *d_w64 = nullptr;
+           *d_s64 = nullptr, *d_w64 = nullptr, *d_kp = nullptr;
     float *d_v32 = nullptr, *d_s32 = nullptr, *d_w32 = nullptr;
     void *counter_grid = nullptr;
-    if ((rc = upload(p, &d_cells, cells)) || (rc = upload(p, &d_items, item_cell)) || (rc = upload(p, &d_v64, v64)) ||
+    std::vector<double> kpoly(pgb::kPolyCoefF64, 0.0);
+    kernel_poly(B->w, B->beta, kpoly.data());
+    if ((rc = upload(p, &d_cells, cells)) || (rc = upload(p, &d_kp, kpoly)) || (rc = upload(p, &d_items, item_cell)) || (rc = upload(p, &d_v64, v64)) ||
         (rc = upload(p, &d_v32, v32)) || (rc = upload(p, &d_sa, scale_a)) || (rc = upload(p, &d_im, inv_mu2)) ||
         (rc = upload(p, &d_R, R)) || (rc = upload(p, &d_E, E)) || (rc = upload(p, &d_D, D)) ||
         (rc = upload(p, &d_s64, sig64)) || (rc = upload(p, &d_s32, sig32)) || (rc = upload(p, &d_w64, wsig64)) ||
@@ -764,6 +769,7 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
     a.sig32 = d_s32;
     a.wsig64 = d_w64;
     a.wsig32 = d_w32;
+    a.kpoly = d_kp;
 
     // ---- persistent spreading launch shape
     cudaDeviceProp prop;
@@ -773,13 +779,18 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
         return nullptr;
     }
     B->spread_smem = (size_t)max_cells_tile * (f32 ? 4 : 8);  // FP32: one word per cell; FP64: a double
-    if (B->spread_smem + 1024 > prop.sharedMemPerBlockOptin) {
+    // the kernel's static shared memory: the current cell's descriptor and spreading arguments,
+    // FP64: the kernel polynomial
+    const size_t static_smem =
+        sizeof(pgb::CellDesc) + sizeof(pgb::SpreadArgs) + 64 + (f32 ? 0 : sizeof(double) * pgb::kPolyCoefF64);
+    if (B->spread_smem + static_smem > prop.sharedMemPerBlockOptin) {
         set_error(PG_ERR_ARG, "largest cell's folded grid (%d cells) does not fit shared memory", max_cells_tile);
         free_plan(p);
         return nullptr;
     }
     const int max_threads = f32 ? pgb::kBatchThreadsF32 : pgb::kMaxThreadsF64;
-    int per_sm = (int)(prop.sharedMemPerMultiprocessor / (B->spread_smem + 2048 + prop.reservedSharedMemPerBlock));
+    int per_sm = (int)(prop.sharedMemPerMultiprocessor /
+                       (B->spread_smem + static_smem + 1024 + prop.reservedSharedMemPerBlock));
     per_sm = std::max(per_sm, 1);
     if (o.spread_blocks_per_sm > 0) per_sm = std::min(per_sm, o.spread_blocks_per_sm);
     B->spread_threads = (o.spread_threads > 0) ? o.spread_threads

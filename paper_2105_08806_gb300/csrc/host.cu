@@ -88,6 +88,48 @@ int width_for(double tol, double sigma)
     return std::max(w, pgb::kMinWidth);
 }
 
+// Tap a of the kernel as a function of the offset y in [-1, 1]: t = (y + 1 + 2a - w)/w.
+static long double kernel_tap(int w, double beta, int a, long double y)
+{
+    const long double t = (y + 1.0L + 2.0L * a - w) / w;
+    const long double om = 1.0L - t * t;
+    return om > 0.0L ? expl((long double)beta * (sqrtl(om) - 1.0L)) : 0.0L;
+}
+
+// Interpolate each tap at the P = kernel_poly_terms(w) Chebyshev points of [-1, 1] (coefficients
+// of T_j by the discrete cosine sums, then expanded in powers of y through
+// T_{j+1} = 2y T_j - T_{j-1}), all in long double; split into even and odd parts.
+void kernel_poly(int w, double beta, double *c)
+{
+    const int P = pgb::kernel_poly_terms(w), NE = (P + 1) / 2, NO = P / 2;
+    const long double pi = 3.141592653589793238462643383279502884L;
+    std::vector<long double> g(P), cheb(P), mono(P), Tm(P), T0(P), T1(P);
+    for (int a = 0; a < (w + 1) / 2; ++a) {
+        for (int k = 0; k < P; ++k) g[k] = kernel_tap(w, beta, a, cosl(pi * (k + 0.5L) / P));
+        for (int j = 0; j < P; ++j) {
+            long double acc = 0.0L;
+            for (int k = 0; k < P; ++k) acc += g[k] * cosl(pi * j * (k + 0.5L) / P);
+            cheb[j] = acc * (j == 0 ? 1.0L : 2.0L) / P;
+        }
+        std::fill(mono.begin(), mono.end(), 0.0L);
+        std::fill(T0.begin(), T0.end(), 0.0L);
+        std::fill(T1.begin(), T1.end(), 0.0L);
+        T0[0] = 1.0L;  // T_0
+        if (P > 1) T1[1] = 1.0L;  // T_1
+        for (int j = 0; j < P; ++j) {
+            const std::vector<long double> &Tj = (j == 0) ? T0 : T1;
+            for (int k = 0; k < P; ++k) mono[k] += cheb[j] * Tj[k];
+            if (j >= 1) {  // T_{j+1} = 2 y T_j - T_{j-1} into Tm, then shift
+                for (int k = 0; k < P; ++k) Tm[k] = (k > 0 ? 2.0L * T1[k - 1] : 0.0L) - T0[k];
+                T0 = T1;
+                T1 = Tm;
+            }
+        }
+        for (int k = 0; k < NE; ++k) c[a * P + k] = (double)mono[2 * k];
+        for (int k = 0; k < NO; ++k) c[a * P + NE + k] = (double)mono[2 * k + 1];
+    }
+}
+
 // psi_hat(k) = int psi(x) cos(k x) dx with psi(x) = exp(beta (sqrt(1 - (x/alpha)^2) - 1)),
 // |x| < alpha = w pi / n.  With x = alpha sin(theta) the integrand is smooth:
 // alpha int_{-pi/2}^{pi/2} exp(beta (cos theta - 1)) cos(k alpha sin theta) cos theta dtheta.

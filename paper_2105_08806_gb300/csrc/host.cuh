@@ -53,6 +53,9 @@ int width_for(double tol, double sigma);
 double kernel_beta(int w, double sigma);
 // Even periodic grid size n >= sigma (2N + 1).
 int grid_size(int N, double sigma);
+// Piecewise polynomial form of the kernel for the FP64 spreading kernels: ceil(w/2) blocks of
+// kernel_poly_terms(w) coefficients (layout of SpreadArgs::kpoly).
+void kernel_poly(int w, double beta, double *c);
 // psi_hat(k), k = 0..N, of the exponential-of-semicircle kernel of width w on a grid of n cells.
 std::vector<double> kernel_ft(int N, int w, double beta, int n);
 // Sphere quadrature (points M x d, weights M), Section 4.1.
@@ -122,6 +125,7 @@ struct pg_boltz_plan_s {
     float *a32 = nullptr;
     double *h = nullptr, *Qplus = nullptr, *Qlast = nullptr, *mom = nullptr;
     int *carry = nullptr;      // FP32 spreading: per-block carry counters
+    double *kpoly = nullptr;   // FP64 spreading: the kernel polynomial (kPolyCoefF64 doubles)
     double *ub = nullptr;      // N^d per-node strength bounds
     double *bound = nullptr;   // scalar B >= sum_p |q_p| (follows the grid in one allocation)
     unsigned long long *grid = nullptr;  // folded grid, int64 fixed point

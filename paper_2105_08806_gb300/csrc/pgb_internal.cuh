@@ -15,6 +15,12 @@ namespace pgb {
 // Angular factor of the collision kernel B(|g|, cos theta) = Bconst |g|^gamma b(cos theta)
 // (Eq. collision_form), b(c) = sum_{p < n} c_p c^p; n = 0 is the VHS kernel (b = 1).
 constexpr int kMaxAngular = 8;
+// Coefficients of the FP64 spreading kernel's piecewise polynomial form (kernel_poly on the host):
+// ceil(w/2) taps of kernel_poly_terms(w) each, for widths up to 16.  Degree w interpolates each tap
+// to about the kernel's own truncation error exp(-beta) at the default oversampling 2 for w >= 7;
+// narrower kernels take two more terms, which keeps oversampling up to 4 within a few times it.
+__host__ __device__ constexpr int kernel_poly_terms(int w) { return w < 12 ? w + 3 : w + 1; }
+constexpr int kPolyCoefF64 = 8 * 17;
 struct Angular {
     int n;
     double c[kMaxAngular];
@@ -50,6 +56,11 @@ struct SpreadArgs {
     int nang_even;        // terms of ang_even; 0: VHS kernel (no angular factor)
     double ang_even[kMaxAngular / 2];
     double angmax;        // sum_k |ang_even[k]| >= |b_e(c)| on [-1, 1] (1 for VHS)
+    // FP64 kernel weights: tap a (< ceil(w/2)) of a point at offset y in [-1, 1] within its cell is
+    // E_a(y^2) + y O_a(y^2), and tap w-1-a is E_a(y^2) - y O_a(y^2); with P = kernel_poly_terms(w),
+    // kpoly[a P + k] (device, kPolyCoefF64 doubles) holds the (P+1)/2 coefficients of E_a, then
+    // the P/2 of O_a, lowest power first
+    const double *kpoly;
 };
 
 // Node pairs the spreading kernels walk: each unordered pair {i, j} once (the two orders add the
@@ -95,6 +106,9 @@ cudaError_t launch_spread_f64_d3_ang(const SpreadArgs &a, int w, int blocks, int
 // Highest kernel width with a compiled spreading kernel for each type.
 constexpr int kMaxWidthF32 = 10;
 constexpr int kMaxWidthF64 = 16;
+static_assert(kPolyCoefF64 >= ((kMaxWidthF64 + 1) / 2) * kernel_poly_terms(kMaxWidthF64) &&
+                  kPolyCoefF64 >= 6 * kernel_poly_terms(11),
+              "kernel polynomial storage");
 constexpr int kMinWidth = 2;
 // Largest spreading block for each type (the kernels' launch bounds).
 constexpr int kMaxThreadsF32 = 1024;

@@ -115,8 +115,9 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
     // block tiles: rows of (nf^(d-2) x ncol) cells, the last axis padded with unfolded columns
     const int cpad = pgb::tile_col_pad(p->w), ncol = p->nf + 2 * cpad;
     const size_t plane = (size_t)ipow(p->nf, d - 2) * ncol;
-    const size_t max_smem = prop.sharedMemPerBlockOptin - 1024;  // leave room for the kernels' static shared memory
     const bool f32 = (p->prec == PG_PREC_FP32);
+    // leave room for the kernels' static shared memory (FP64: the kernel polynomial)
+    const size_t max_smem = prop.sharedMemPerBlockOptin - 1024 - (f32 ? 0 : sizeof(double) * pgb::kPolyCoefF64);
     const int max_threads = f32 ? pgb::kMaxThreadsF32 : pgb::kMaxThreadsF64;
     int rows_fit = (int)std::min<size_t>(p->nf, max_smem / (plane * elem));
     size_t qbytes = 0;
@@ -159,9 +160,18 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
     const long long need = ((p->npairs + p->spread_threads - 1) / p->spread_threads) * p->nslab;
     blocks = std::min(blocks, need);
     p->spread_blocks = (int)blocks;
+    // the pair schedule permutes thread starts by a multiplier prime to every smaller count
+    if ((blocks / p->nslab) * p->spread_threads >= 1000003)
+        return set_error(PG_ERR_ARG, "spreading launch of %lld threads per slab exceeds the pair schedule's range",
+                         (blocks / p->nslab) * p->spread_threads);
     const long long tile_cells = (long long)p->rows_per_slab * (long long)plane;
     if (f32) {  // per-block carry counters of the FP32 tiles (global memory, cleared by each block)
         int rc2 = dev_alloc(p, (void **)&p->carry, (size_t)blocks * tile_cells * sizeof(int));
+        if (rc2) return rc2;
+    } else {
+        std::vector<double> kp(pgb::kPolyCoefF64, 0.0);
+        kernel_poly(p->w, p->beta, kp.data());
+        int rc2 = upload(p, &p->kpoly, kp);
         if (rc2) return rc2;
     }
 
@@ -200,6 +210,7 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
     ka.nang_even = p->ang.n ? (p->ang.n + 1) / 2 : 0;
     for (int k = 0; k < ka.nang_even; ++k) ka.ang_even[k] = p->ang.c[2 * k];
     ka.angmax = p->angmax;
+    ka.kpoly = p->kpoly;
     return PG_OK;
 }
 
@@ -612,6 +623,25 @@ PG_API int pg_boltz_adaptive_scale(int N, double L, int map_log, double *S_out)
     if (!std::isfinite(L) || L <= 0.0) return set_error(PG_ERR_ARG, "L must be finite and > 0");
     const double phi = kPi / (N + 1);
     *S_out = map_log ? L / std::atanh(std::cos(phi)) : L * std::tan(phi);
+    return PG_OK;
+}
+
+PG_API int pg_boltz_kernel_poly(int w, double upsampfac, double *coef_out, int capacity, int *terms_out,
+                                double *beta_out)
+{
+    if (!coef_out || !terms_out || !beta_out) return set_error(PG_ERR_ARG, "NULL argument");
+    if (w < pgb::kMinWidth || w > pgb::kMaxWidthF64)
+        return set_error(PG_ERR_ARG, "w must be in [%d, %d] (got %d)", pgb::kMinWidth, pgb::kMaxWidthF64, w);
+    const double sigma = (upsampfac == 0.0) ? 2.0 : upsampfac;
+    if (!(sigma >= 1.5 && sigma <= 4.0)) return set_error(PG_ERR_ARG, "upsampfac must be in [1.5, 4] (got %g)", upsampfac);
+    const int P = pgb::kernel_poly_terms(w), need = (w + 1) / 2 * P;
+    if (capacity < need) return set_error(PG_ERR_ARG, "capacity %d below %d coefficients", capacity, need);
+    double c[pgb::kPolyCoefF64];
+    const double beta = kernel_beta(w, sigma);
+    kernel_poly(w, beta, c);
+    std::copy(c, c + need, coef_out);
+    *terms_out = P;
+    *beta_out = beta;
     return PG_OK;
 }
 

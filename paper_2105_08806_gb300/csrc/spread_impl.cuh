@@ -50,11 +50,7 @@ struct Fn;
 template <>
 struct Fn<float> {
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
-    // sqrt of x > 0 through the reciprocal square root (a few ulp; enough for FP32 weights)
-    static __device__ __forceinline__ float sqrt_pos(float x) { return x * rsqrtf(x); }
-    static __device__ __forceinline__ float exp_(float x) { return __expf(x); }
     static __device__ __forceinline__ float atan2_(float y, float x) { return atan2f(y, x); }
-    static __device__ __forceinline__ float sinh_(float x) { return sinhf(x); }
     static __device__ __forceinline__ float cosh_(float x) { return coshf(x); }
     static __device__ __forceinline__ float pow_(float x, float y) { return powf(x, y); }
     static __device__ __forceinline__ float floor_(float x) { return floorf(x); }
@@ -63,10 +59,7 @@ struct Fn<float> {
 template <>
 struct Fn<double> {
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
-    static __device__ __forceinline__ double sqrt_pos(double x) { return sqrt(x); }
-    static __device__ __forceinline__ double exp_(double x) { return exp(x); }
     static __device__ __forceinline__ double atan2_(double y, double x) { return atan2(y, x); }
-    static __device__ __forceinline__ double sinh_(double x) { return sinh(x); }
     static __device__ __forceinline__ double cosh_(double x) { return cosh(x); }
     static __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
     static __device__ __forceinline__ double floor_(double x) { return floor(x); }
@@ -96,23 +89,56 @@ __device__ __forceinline__ int fold_cell(int u, int n, bool simple)
 template <int W>
 __device__ __forceinline__ int kernel_weights_f32(const SpreadArgs &p, float x, float *wt);
 
+// FP64: psi of tap a is a polynomial (kernel_poly_terms(w) terms) in the point's offset
+// y = 2 (s - x) + w - 1 in (-1, 1] (t = (y + 1 + 2a - w)/w), fitted on the host.  Taps a and
+// w-1-a mirror each other (t_{w-1-a}(-y) = -t_a(y) and psi is even), so one even part E_a(y^2)
+// and one odd part y O_a(y^2) give both: about w + 2 FMAs per tap pair instead of an exp and a
+// sqrt per tap.
+// The coefficients sit in shared memory (s_kpoly, filled by load_kernel_poly at the start of each
+// FP64 spreading kernel) and are read through an offset the compiler cannot see to be zero: read
+// in place they cost one shared load each, whereas hoisted out of the point loops they would
+// hold ~4 registers per tap and coefficient (spills at w >= 15).
+__shared__ double s_kpoly[kPolyCoefF64];
+
+__device__ __forceinline__ void load_kernel_poly(const double *kpoly)
+{
+    for (int k = threadIdx.x; k < kPolyCoefF64; k += blockDim.x) s_kpoly[k] = kpoly[k];
+}
+
+template <int W>
+__device__ __forceinline__ int kernel_weights_f64(double x, double *wt)
+{
+    constexpr int P = kernel_poly_terms(W), NE = (P + 1) / 2, NO = P / 2;
+    int zero;
+    asm volatile("mov.b32 %0, 0;" : "=r"(zero));
+    const double *cb = s_kpoly + zero;
+    const int s = (int)floor(x - 0.5 * W) + 1;
+    const double y = fma(2.0, double(s) - x, double(W - 1));
+    const double u = y * y;
+#pragma unroll
+    for (int a = 0; a < (W + 1) / 2; ++a) {
+        const double *c = cb + a * P;
+        double e = c[NE - 1];
+#pragma unroll
+        for (int k = NE - 2; k >= 0; --k) e = fma(e, u, c[k]);
+        if (2 * a + 1 == W) {  // middle tap of an odd width: even in y
+            wt[a] = e;
+        } else {
+            double o = c[NE + NO - 1];
+#pragma unroll
+            for (int k = NO - 2; k >= 0; --k) o = fma(o, u, c[NE + k]);
+            wt[a] = fma(y, o, e);
+            wt[W - 1 - a] = fma(-y, o, e);
+        }
+    }
+    return s;
+}
+
 template <typename T, int W>
 __device__ __forceinline__ int kernel_weights(const SpreadArgs &p, T x, T *wt)
 {
-    if constexpr (sizeof(T) == 4) {
-        return kernel_weights_f32<W>(p, x, wt);
-    } else {
-        const int s = (int)Fn<T>::floor_(x - T(0.5 * W)) + 1;
-        const T inv_hw = T(2.0 / W);
-        const T beta = T(p.beta);
-#pragma unroll
-        for (int a = 0; a < W; ++a) {
-            const T t = (T(s + a) - x) * inv_hw;
-            const T one_m = T(1) - t * t;
-            wt[a] = one_m > T(0) ? Fn<T>::exp_(beta * (Fn<T>::sqrt_pos(one_m) - T(1))) : T(0);
-        }
-        return s;
-    }
+    if constexpr (sizeof(T) == 4) return kernel_weights_f32<W>(p, x, wt);
+    else return kernel_weights_f64<W>(x, wt);
 }
 
 // The weights and the folded cells fold(s + a) of one axis.
@@ -323,16 +349,20 @@ struct SplitTile {
     }
     // |x| < 2^31 known in advance
     __device__ __forceinline__ void add_small(int c, float x) const { add32(c, __float2int_rn(x)); }
+    // the contribution a b
+    __device__ __forceinline__ void add_product(int c, float a, float b) const { add(c, a * b); }
+    __device__ __forceinline__ void add_product_small(int c, float a, float b) const { add_small(c, a * b); }
     // the cell's sum in tile units
     __device__ __forceinline__ long long value(int c) const { return (long long)carry[c] * 4294967296LL + lo[c]; }
 };
 struct DoubleTile {  // FP64 path: FP64 partial sums
     double *v;
-    __device__ __forceinline__ void add(int c, double x) const
-    {
-        if (x != 0.0) atomicAdd(v + c, x);
-    }
-    __device__ __forceinline__ void add_small(int c, double x) const { add(c, x); }
+    // v[c] += a b (the library's shared-memory FP64 atomic add; a hand-written compare-and-swap
+    // loop around one fused multiply-add measured 2-8x slower).  No test for a zero product: the
+    // polynomial kernel weights are not zero at the support's ends as the exact kernel's are,
+    // and a zero-strength point is skipped whole (spread_point).
+    __device__ __forceinline__ void add_product(int c, double a, double b) const { atomicAdd(v + c, a * b); }
+    __device__ __forceinline__ void add_product_small(int c, double a, double b) const { add_product(c, a, b); }
 };
 
 // Point m of pair P: grid coordinates x (one grid cell = 1, x = z n / (2 pi)) and strength q in
@@ -393,6 +423,9 @@ template <typename T, int D, int W, typename Tile, bool SMALL, bool SLAB>
 __device__ __forceinline__ void spread_point(const SpreadArgs &p, const T *x, T q, const Tile &tile, int row_lo,
                                              int nrows, int plane)
 {
+    if constexpr (sizeof(T) == 8) {
+        if (q == T(0)) return;  // FP64 tiles add every product (DoubleTile)
+    }
     T w0[W];
     int r0[W];
     axis_weights<T, W>(p, x[0], w0, r0);
@@ -415,8 +448,8 @@ __device__ __forceinline__ void spread_point(const SpreadArgs &p, const T *x, T 
             const int row = r0[a] * plane + cb;
 #pragma unroll
             for (int c = 0; c < W; ++c) {
-                if constexpr (SMALL) tile.add_small(row + c, w0[a] * wl[c]);
-                else tile.add(row + c, w0[a] * wl[c]);
+                if constexpr (SMALL) tile.add_product_small(row + c, w0[a], wl[c]);
+                else tile.add_product(row + c, w0[a], wl[c]);
             }
         }
     } else {
@@ -434,8 +467,8 @@ __device__ __forceinline__ void spread_point(const SpreadArgs &p, const T *x, T 
                 const int line = row + c1[b];
 #pragma unroll
                 for (int c = 0; c < W; ++c) {
-                    if constexpr (SMALL) tile.add_small(line + c, wab * wl[c]);
-                    else tile.add(line + c, wab * wl[c]);
+                    if constexpr (SMALL) tile.add_product_small(line + c, wab, wl[c]);
+                    else tile.add_product(line + c, wab, wl[c]);
                 }
             }
         }
@@ -581,17 +614,19 @@ __device__ __forceinline__ SlabGeom slab_geometry(const SpreadArgs &p, int D)
     return g;
 }
 
-// Pair numbering: the threads of one slab cover the pairs with stride `nthr`.  Lanes of a
-// warp take pairs nwarps apart (lane-major numbering), so the 32 points a warp spreads at
-// once come from unrelated (i, j) and rarely hit the same grid cells; neighbouring pairs
-// produce neighbouring points and would serialise the shared-memory atomics.
+// Pair numbering: the threads of one slab cover the pairs with stride `nthr`, thread r of the
+// slab (r = 32 warp + lane) starting at (r A) mod nthr with A = 1000003, a prime above any
+// thread count (at most SMs x 2048), so the starts are a permutation of 0..nthr-1.  Lanes of a
+// warp then take pairs A apart modulo nthr: unrelated (t, i), whose 32 points rarely hit the
+// same grid cells.  Neighbouring pairs produce neighbouring points and would serialise the
+// shared-memory atomics; a plain lane stride of nwarps keeps the lanes on one node column
+// whenever nwarps and N share a power of two.
 __device__ __forceinline__ void pair_schedule(const SpreadArgs &p, long long &first, long long &nthr)
 {
     const long long groups = gridDim.x / p.nslab;
     nthr = groups * blockDim.x;
-    const long long nwarps = nthr >> 5;
-    const long long gwarp = (long long)(blockIdx.x / p.nslab) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    first = (long long)(threadIdx.x & 31) * nwarps + gwarp;
+    const long long r = (long long)(blockIdx.x / p.nslab) * blockDim.x + threadIdx.x;
+    first = (r * 1000003LL) % nthr;
 }
 
 template <int D, int W, bool ANG>
@@ -650,6 +685,7 @@ __global__ void __launch_bounds__(kMaxThreadsF64) k_spread_f64(const __grid_cons
     if (G.nrows <= 0) return;  // uniform over the block
     DoubleTile tile{reinterpret_cast<double *>(smem_raw)};
     for (int c = threadIdx.x; c < G.ncell; c += blockDim.x) tile.v[c] = 0.0;
+    load_kernel_poly(p.kpoly);
     __syncthreads();
     const double Bnd = *p.bound;
     const int Eg = global_exponent(Bnd);

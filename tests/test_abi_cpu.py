@@ -107,3 +107,66 @@ def test_adaptive_scale_rejects_bad_arguments(L):
     assert L.pg_boltz_adaptive_scale(8, 0.0, 0, ctypes.byref(out)) == _lib.PG_ERR_ARG
     assert L.pg_boltz_adaptive_scale(8, float("inf"), 1, ctypes.byref(out)) == _lib.PG_ERR_ARG
     assert L.pg_boltz_adaptive_scale(8, 5.0, 0, None) == _lib.PG_ERR_ARG
+
+
+def _psi(t, beta):
+    """Exponential-of-semicircle kernel psi(t) = exp(beta (sqrt(1 - t^2) - 1)), |t| < 1, else 0,
+    in long double (in double the rounding of beta (sqrt - 1) alone is a few 1e-15)."""
+    import numpy as np
+    t = np.asarray(t, dtype=np.longdouble)
+    om = 1 - t * t
+    return np.where(om > 0, np.exp(np.longdouble(beta) * (np.sqrt(np.maximum(om, 0)) - 1)), 0)
+
+
+def _poly_taps(w, P, c, y):
+    """All w taps from the even/odd coefficient blocks (the FP64 spreading kernels' evaluation),
+    summed in long double so that the comparison sees the fit, not this sum's rounding."""
+    import numpy as np
+    NE, NO = (P + 1) // 2, P // 2
+    y = np.asarray(y, dtype=np.longdouble)
+    c = [np.longdouble(v) for v in c]
+    u = y * y
+    taps = np.zeros((w, y.size), dtype=np.longdouble)
+    for a in range((w + 1) // 2):
+        blk = c[a * P:(a + 1) * P]
+        e = np.zeros_like(y)
+        for k in reversed(blk[:NE]):
+            e = e * u + k
+        o = np.zeros_like(y)
+        for k in reversed(blk[NE:NE + NO]):
+            o = o * u + k
+        taps[a] = e + y * o if 2 * a + 1 != w else e
+        taps[w - 1 - a] = e - y * o if 2 * a + 1 != w else e
+    return taps
+
+
+@pytest.mark.parametrize("sigma", [1.5, 2.0, 4.0])
+@pytest.mark.parametrize("w", range(2, 17))
+def test_kernel_poly_matches_kernel_definition(L, w, sigma):
+    """Every tap of the polynomial form against psi at the tap's own t = (s + a - x) 2/w for
+    points spread over a cell: within the kernel's own size at its support edge, exp(-beta)."""
+    import numpy as np
+    beta, P, c = _lib.kernel_poly(w, sigma)
+    assert beta == pytest.approx(0.97 * np.pi * (1 - 0.5 / sigma) * w, rel=1e-15)
+    assert P == (w + 3 if w < 12 else w + 1) and len(c) == (w + 1) // 2 * P
+    x = 40.0 + np.linspace(0.0, 1.0, 1001, endpoint=False) + 0.5e-3
+    s = np.floor(x - 0.5 * w) + 1
+    y = 2.0 * (s - x) + (w - 1)  # exact: s - x and the sums are representable
+    assert y.min() > -1 and y.max() <= 1
+    taps = _poly_taps(w, P, c, y)
+    exact = np.stack([_psi((s + a - x) * 2.0 / w, beta) for a in range(w)])
+    err = float(np.abs(taps - exact).max())
+    bound = (0.6 if (sigma == 2.0 and w >= 6) else 4.0) * np.exp(-beta) + 3e-16
+    assert err <= bound, (w, sigma, err, np.exp(-beta))
+
+
+def test_kernel_poly_rejects_bad_arguments(L):
+    buf = (ctypes.c_double * 136)()
+    P, beta = ctypes.c_int(0), ctypes.c_double(0.0)
+    args = lambda w, sig, cap: (w, sig, buf, cap, ctypes.byref(P), ctypes.byref(beta))
+    assert L.pg_boltz_kernel_poly(*args(1, 2.0, 136)) == _lib.PG_ERR_ARG
+    assert L.pg_boltz_kernel_poly(*args(17, 2.0, 136)) == _lib.PG_ERR_ARG
+    assert L.pg_boltz_kernel_poly(*args(8, 1.2, 136)) == _lib.PG_ERR_ARG
+    assert L.pg_boltz_kernel_poly(*args(16, 2.0, 135)) == _lib.PG_ERR_ARG
+    assert L.pg_boltz_kernel_poly(16, 2.0, None, 136, ctypes.byref(P), ctypes.byref(beta)) == _lib.PG_ERR_ARG
+    assert L.pg_boltz_kernel_poly(*args(16, 0.0, 136)) == _lib.PG_OK and P.value == 17
