@@ -16,7 +16,10 @@
 //   r = 1 (algebraic):   cos z = v/sqrt(S^2+v^2), sin z = S/sqrt(S^2+v^2)
 //                        -> z = atan2(S, v),      mu^-2 = (S^2 + v^2)/S
 //   r = 0 (logarithmic): cos z = tanh(v/S), sin z = sech(v/S)
-//                        -> z = atan2(1, sinh(v/S)), mu^-2 = S cosh(v/S)
+//                        -> z = 2 atan(e^(-v/S)), mu^-2 = S cosh(v/S)
+//                           (FP64: from e = e^-|v/S| <= 1, z = 2 atan(e) or pi - 2 atan(e))
+// Kernel values: FP32 from ex2.approx / rsqrt.approx of the definition; FP64 from per-tap
+// polynomials fitted on the host (kernel_weights_f64).
 //
 // Accumulation:
 //  - the global folded grid holds int64 values in units of 2^-Eg, where B >= sum_p |q_p|
