@@ -329,29 +329,36 @@ __device__ __forceinline__ int tile_to_grid_cell(int c, int D, int nf, int ncol,
 constexpr int kTileBits = 14;
 
 struct SplitTile {
-    int *lo;     // tile words (shared memory)
-    int *carry;  // this block's carry counters (global memory, same layout)
-    __device__ __forceinline__ void add32(int c, int v) const
+    int *lo;       // tile words (shared memory)
+    int *carry;    // this block's carry counters (global memory, same layout)
+    int sgn = 1;   // sign of the current point's contributions (spread_point, with_sign)
+    // The tile for the contributions of one point of strength q: every kernel weight is >= 0, so
+    // they all have the sign of q, and a word wraps only in the direction of its addend's sign,
+    // so the counter moves by the point's sign (one value per point, not one per contribution).
+    __device__ __forceinline__ SplitTile with_sign(float q) const { return SplitTile{lo, carry, q < 0.0f ? -1 : 1}; }
+    // v of sign d (or zero)
+    __device__ __forceinline__ void add32(int c, int v, int d) const
     {
         const int o = atomicAdd(lo + c, v);
         const int r = (int)((unsigned)o + (unsigned)v);
-        if (((o ^ r) & (v ^ r)) < 0) atomicAdd(carry + c, v < 0 ? -1 : 1);
+        if (((o ^ r) & (v ^ r)) < 0) atomicAdd(carry + c, d);
     }
     __device__ __forceinline__ void add64(int c, long long x) const
     {
         const int xl = (int)(unsigned)(unsigned long long)x;  // low word, signed
         const long long xh = (x - xl) >> 32;                   // exact: x - xl is a multiple of 2^32
-        add32(c, xl);
+        add32(c, xl, xl < 0 ? -1 : 1);
         if (xh) atomicAdd(carry + c, (int)xh);
     }
-    // Zero contributions are added too: a branch around them costs more than the atomic.
+    // x of sign sgn.  Zero contributions are added too: a branch around them costs more than the
+    // atomic.
     __device__ __forceinline__ void add(int c, float x) const
     {
-        if (fabsf(x) < 2147483648.0f) add32(c, __float2int_rn(x));
+        if (fabsf(x) < 2147483648.0f) add32(c, __float2int_rn(x), sgn);
         else add64(c, __float2ll_rn(x));
     }
     // |x| < 2^31 known in advance
-    __device__ __forceinline__ void add_small(int c, float x) const { add32(c, __float2int_rn(x)); }
+    __device__ __forceinline__ void add_small(int c, float x) const { add32(c, __float2int_rn(x), sgn); }
     // the contribution a b
     __device__ __forceinline__ void add_product(int c, float a, float b) const { add(c, a * b); }
     __device__ __forceinline__ void add_product_small(int c, float a, float b) const { add_small(c, a * b); }
@@ -360,6 +367,7 @@ struct SplitTile {
 };
 struct DoubleTile {  // FP64 path: FP64 partial sums
     double *v;
+    __device__ __forceinline__ DoubleTile with_sign(double) const { return *this; }
     // v[c] += a b (the library's shared-memory FP64 atomic add; a hand-written compare-and-swap
     // loop around one fused multiply-add measured 2-8x slower).  No test for a zero product: the
     // polynomial kernel weights are not zero at the support's ends as the exact kernel's are,
@@ -423,12 +431,13 @@ __device__ __forceinline__ void make_point(const SpreadArgs &p, const PairData<T
 // holds a slab of the grid's rows and rows outside it are skipped; otherwise it holds every row
 // (row_lo = 0, nrows = n/2 + 1).
 template <typename T, int D, int W, typename Tile, bool SMALL, bool SLAB>
-__device__ __forceinline__ void spread_point(const SpreadArgs &p, const T *x, T q, const Tile &tile, int row_lo,
+__device__ __forceinline__ void spread_point(const SpreadArgs &p, const T *x, T q, const Tile &tile_all, int row_lo,
                                              int nrows, int plane)
 {
     if constexpr (sizeof(T) == 8) {
         if (q == T(0)) return;  // FP64 tiles add every product (DoubleTile)
     }
+    const Tile tile = tile_all.with_sign(q);
     T w0[W];
     int r0[W];
     axis_weights<T, W>(p, x[0], w0, r0);
