@@ -732,7 +732,6 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
     a.Bconst = 1.0 / (d == 2 ? 2.0 * kPi : 4.0 * kPi);
     a.beta = B->beta;
     a.screen_eps = o.screen ? 0.05 * o.tol : 0.0;
-    int rc;
     pgb::CellDesc *d_cells = nullptr;
     int *d_items = nullptr;
     double *d_v64 = nullptr, *d_sa = nullptr, *d_im = nullptr, *d_R = nullptr, *d_E = nullptr, *d_D = nullptr,
@@ -741,16 +740,15 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
     void *counter_grid = nullptr;
     std::vector<double> kpoly(pgb::kPolyCoefF64, 0.0);
     kernel_poly(B->w, B->beta, kpoly.data());
-    if ((rc = upload(p, &d_cells, cells)) || (rc = upload(p, &d_kp, kpoly)) || (rc = upload(p, &d_items, item_cell)) || (rc = upload(p, &d_v64, v64)) ||
-        (rc = upload(p, &d_v32, v32)) || (rc = upload(p, &d_sa, scale_a)) || (rc = upload(p, &d_im, inv_mu2)) ||
-        (rc = upload(p, &d_R, R)) || (rc = upload(p, &d_E, E)) || (rc = upload(p, &d_D, D)) ||
-        (rc = upload(p, &d_s64, sig64)) || (rc = upload(p, &d_s32, sig32)) || (rc = upload(p, &d_w64, wsig64)) ||
-        (rc = upload(p, &d_w32, wsig32)) || (rc = dev_alloc(p, (void **)&a.a64, a_off * 8)) ||
-        (rc = dev_alloc(p, (void **)&a.a32, a_off * 4)) || (rc = dev_alloc(p, (void **)&a.h, a_off * 8)) ||
-        (rc = dev_alloc(p, (void **)&a.Bcell, (size_t)ncell * 8)) ||
-        (rc = dev_alloc(p, (void **)&a.Tcell, (size_t)ncell * 8)) ||
-        (rc = dev_alloc(p, &counter_grid, 256 + (size_t)grid_off * 8)) ||
-        (rc = dev_alloc(p, (void **)&a.scratch, (size_t)s_off * 8))) {
+    // each failing call has recorded its error for pg_boltz_last_error
+    if (upload(p, &d_cells, cells) || upload(p, &d_kp, kpoly) || upload(p, &d_items, item_cell) ||
+        upload(p, &d_v64, v64) || upload(p, &d_v32, v32) || upload(p, &d_sa, scale_a) || upload(p, &d_im, inv_mu2) ||
+        upload(p, &d_R, R) || upload(p, &d_E, E) || upload(p, &d_D, D) || upload(p, &d_s64, sig64) ||
+        upload(p, &d_s32, sig32) || upload(p, &d_w64, wsig64) || upload(p, &d_w32, wsig32) ||
+        dev_alloc(p, (void **)&a.a64, a_off * 8) || dev_alloc(p, (void **)&a.a32, a_off * 4) ||
+        dev_alloc(p, (void **)&a.h, a_off * 8) || dev_alloc(p, (void **)&a.Bcell, (size_t)ncell * 8) ||
+        dev_alloc(p, (void **)&a.Tcell, (size_t)ncell * 8) || dev_alloc(p, &counter_grid, 256 + (size_t)grid_off * 8) ||
+        dev_alloc(p, (void **)&a.scratch, (size_t)s_off * 8)) {
         free_plan(p);
         return nullptr;
     }
@@ -805,11 +803,11 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
     a.carry = nullptr;
     a.carry_stride = max_cells_tile;
     B->carry_blocks = B->spread_blocks;
-    if (f32 && (rc = dev_alloc(p, (void **)&a.carry, (size_t)B->spread_blocks * max_cells_tile * sizeof(int)))) {
+    if (f32 && dev_alloc(p, (void **)&a.carry, (size_t)B->spread_blocks * max_cells_tile * sizeof(int))) {
         free_plan(p);
         return nullptr;
     }
-    if ((rc = cuda_check(pgb::batch_spread_attr(f32, d, B->w, B->spread_smem), "batched spread attribute"))) {
+    if (cuda_check(pgb::batch_spread_attr(f32, d, B->w, B->spread_smem), "batched spread attribute")) {
         free_plan(p);
         return nullptr;
     }

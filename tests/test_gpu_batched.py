@@ -172,3 +172,19 @@ def test_autotune_keeps_results_bitwise():
     assert thr in (128, 256, 512, 1024) and blocks % sms == 0 and ms > 0
     assert (info["spread_threads"], info["spread_blocks"]) == (thr, blocks)
     assert torch.equal(Q1, Q2) and torch.equal(Q1, Q3)
+
+
+def test_batched_alloc_failure_injection_leaves_no_plan():
+    """An allocation failing at any of several points of batched plan creation raises and frees
+    what was allocated; the next plan builds normally."""
+    from paper_2105_08806_gb300 import BatchedPlan, PGBoltzError, lib
+    try:
+        for k in (1, 2, 8, 15):
+            lib().pg_boltz_debug_fail_alloc(k)
+            with pytest.raises(PGBoltzError) as ei:
+                BatchedPlan(2, [8, 10], [8, 8], [2.0, 2.0], [0.0, 1.0], 1e-6, precision=PG_PREC_FP32)
+            assert "injected" in str(ei.value)
+    finally:
+        lib().pg_boltz_debug_fail_alloc(0)
+    with BatchedPlan(2, [8, 10], [8, 8], [2.0, 2.0], [0.0, 1.0], 1e-6, precision=PG_PREC_FP32):
+        pass
