@@ -320,7 +320,7 @@ def collide(ftilde, d, N, M, S, gamma, r=1, sphere="auto", modes=None, nthreads=
     return gain - loss
 
 
-PHI_ONE, PHI_V, PHI_V2, PHI_VV, PHI_VV2 = 0, 1, 2, 3, 4
+PHI_ONE, PHI_V, PHI_V2, PHI_VV, PHI_VV2, PHI_V2V2, PHI_V4 = 0, 1, 2, 3, 4, 5, 6
 
 
 def weak(ftilde, d, N, M, S, gamma, phis, r=1, sphere="auto", nthreads=None, angular=None):

@@ -114,7 +114,8 @@ static double angular_b(const prob_t *p, const double *vi, const double *vj, dou
 }
 
 /* Weak-form test functions used for conservation and moment checks:
- * kind 0: 1;  kind 1: v_a;  kind 2: |v|^2;  kind 3: v_a v_b;  kind 4: v_a |v|^2. */
+ * kind 0: 1;  kind 1: v_a;  kind 2: |v|^2;  kind 3: v_a v_b;  kind 4: v_a |v|^2;
+ * kind 5: v_a^2 v_b^2;  kind 6: |v|^4. */
 static double phi_eval(const int *ph, const double *v, int d)
 {
     double n2 = 0.0;
@@ -124,7 +125,9 @@ static double phi_eval(const int *ph, const double *v, int d)
     case 1: return v[ph[1]];
     case 2: return n2;
     case 3: return v[ph[1]] * v[ph[2]];
-    default: return v[ph[1]] * n2;
+    case 4: return v[ph[1]] * n2;
+    case 5: return v[ph[1]] * v[ph[1]] * v[ph[2]] * v[ph[2]];
+    default: return n2 * n2;
     }
 }
 
