@@ -10,12 +10,14 @@
 //
 // The array is a file-scope __device__ variable: every GPU that loads the library holds
 // it until the process exits, and every call shares it.  Host code cannot use the
-// variable's name as a device address, so the first call on each device looks the
-// address up with cudaGetSymbolAddress (with that device current) and caches it.
+// variable's name as a device address, so every call looks the address up with
+// cudaGetSymbolAddress, with the caller's device current.  The lookup allocates nothing, and
+// doing it on every call (instead of caching one address per device) keeps the address right
+// after a device reset or when the caller switches contexts.  On the first call in a context
+// the lookup may load the library's device code (lazy module loading).
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 
 #include "pg_boltz.h"
 #include "pgb_internal.cuh"
@@ -26,10 +28,6 @@ namespace {
 
 constexpr size_t kScratchDoubles = PG_BOLTZ_NOALLOC_SCRATCH_BYTES / sizeof(double);
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_addr_mutex;
-double *g_addr[kMaxDevices] = {nullptr};
 
 int fail(int code, const char *msg) { return pgb::record_error(code, msg); }
 
@@ -56,6 +54,7 @@ __global__ void k_projection_matrix(int N, int Mp, double S, int r, double *P)
 PG_API int pg_boltz_project_noalloc(int d, int N, double S, int map_log, int Mp, const double *fvals_dev,
                                     double *ftilde_dev, void *cuda_stream)
 {
+    pgb::record_error(PG_OK, "");
     if (d != 2 && d != 3) return fail(PG_ERR_ARG, "d must be 2 or 3");
     if (N < 2 || Mp < 1) return fail(PG_ERR_ARG, "need N >= 2 and Mp >= 1");
     if (!(S > 0.0) || !std::isfinite(S)) return fail(PG_ERR_ARG, "S must be positive");
@@ -69,25 +68,12 @@ PG_API int pg_boltz_project_noalloc(int d, int N, double S, int map_log, int Mp,
     if (need > (double)kScratchDoubles)
         return fail(PG_ERR_ARG, "pg_boltz_project_noalloc: (N+1)*Mp + (N+1)*Mp^(d-1) [+ (N+1)^2*Mp in 3D] "
                                 "doubles exceed the static scratch of PG_BOLTZ_NOALLOC_SCRATCH_BYTES");
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
         cudaGetLastError();
-        return fail(PG_ERR_CUDA, "no usable current CUDA device");
+        return fail(PG_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed (no usable current device?)");
     }
-    double *base = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_addr_mutex);
-        if (!g_addr[dev]) {
-            void *ptr = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                return fail(PG_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
-            }
-            g_addr[dev] = static_cast<double *>(ptr);
-        }
-        base = g_addr[dev];
-    }
+    double *base = static_cast<double *>(ptr);
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     double *P = base;
     double *t1 = P + (size_t)(N + 1) * Mp;

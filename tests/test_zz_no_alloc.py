@@ -5,8 +5,10 @@ they already hold, cannot create a plan (plans allocate).  This entry point take
 caller's input and output arrays and keeps its intermediates in a static device array.  The
 test calls it through the C ABI and compares it with the plan-based pg_boltz_project (the
 existing entry point), twice in a row, so that the second call runs on scratch left over by
-the first.  This file is collected last so a stop-at-first-failure run has already run every
-other test.
+the first.  Around the second call (after the plan is destroyed and the first call has loaded
+the library's device code) it also checks that the device's free memory does not change: the
+call allocates nothing.  This file is collected last so a stop-at-first-failure run has already
+run every other test.
 """
 import ctypes
 
@@ -55,9 +57,15 @@ def test_noalloc_projection_matches_plan_twice(L, d, N, S, map_log, Mp):
             ref = torch.empty((N + 1) ** d, dtype=torch.float64, device="cuda")
             plan.project(fv, ref)
         out = torch.full_like(ref, float("nan"))
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         rc = L.pg_boltz_project_noalloc(d, N, S, map_log, Mp, fv.data_ptr(), out.data_ptr(), stream)
         assert rc == 0, L.pg_boltz_last_error().decode()
+        assert L.pg_boltz_last_error().decode() == ""
         torch.cuda.synchronize()
+        free_after = torch.cuda.mem_get_info()[0]
+        if call == 1:  # the first call may load the library's device code in this context
+            assert free_after == free_before, (free_before, free_after)
         assert rel_l2(out.cpu().numpy(), ref.cpu().numpy()) < 1e-12
 
 
@@ -67,3 +75,8 @@ def test_noalloc_rejects_sizes_beyond_the_static_scratch(L):
     rc = L.pg_boltz_project_noalloc(3, 40, 2.0, 0, 200, f.data_ptr(), f.data_ptr(), None)
     assert rc == -1
     assert "static scratch" in L.pg_boltz_last_error().decode()
+    # a later successful call clears the error text
+    g = torch.zeros(9 * 9, dtype=torch.float64, device="cuda")
+    out = torch.empty(3 * 3, dtype=torch.float64, device="cuda")
+    assert L.pg_boltz_project_noalloc(2, 2, 2.0, 0, 9, g.data_ptr(), out.data_ptr(), None) == 0
+    assert L.pg_boltz_last_error().decode() == ""
