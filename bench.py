@@ -64,6 +64,9 @@ def parse():
                     help="run the batched workload on its first K cells only (0: all 4096; for profiling)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD,
                     help="single-plan configuration (the batched run and the CPU baseline go with the default)")
+    ap.add_argument("--sphere-points", type=int, default=0,
+                    help="override the workload's number of sphere points M (0: the workload's own; for "
+                         "profiling the same kernel on a smaller case)")
     return ap.parse_args()
 
 
@@ -275,6 +278,9 @@ def run_ours(args):
     default = args.workload == DEFAULT_WORKLOAD
     w = getattr(Wl, WORKLOADS[args.workload][0])()
     d, N, M, S, gamma = w.d, w.N, w.M, w.S, w.gamma
+    if args.sphere_points > 0:
+        M = args.sphere_points
+        default = False
     stream = torch.cuda.Stream(device=dev)
     plan32 = Plan(d, N, M, S, gamma, args.tol32, precision=PG_PREC_FP32, upsampfac=args.upsampfac)
     plan64 = Plan(d, N, M, S, gamma, 1e-13, precision=PG_PREC_FP64) if args.fp64_steps > 0 else None

@@ -293,6 +293,28 @@ int pg_boltz_batched_autotune(pg_boltz_plan_t *plan, const double *f_packed_dev,
 int pg_boltz_probe_shared_atomics(void *cuda_stream, double *rate_out);
 
 /*
+ * Measured peaks of the whole GPU for the spreading kernels' rooflines (no counterpart in the
+ * paper): rates_out[0] = FP32 fused multiply-adds per second, rates_out[1] = FP64 fused
+ * multiply-adds per second (independent chains in every thread of two 1024-thread blocks per
+ * SM), rates_out[2] = 32-bit integer shared-memory atomic adds per second with every lane of a
+ * warp on its own bank (no conflicts).  rates_out: host array of 3 doubles.  Allocates and frees
+ * 64 bytes; synchronises cuda_stream.  PG_OK, PG_ERR_ARG (NULL) or PG_ERR_CUDA.
+ */
+int pg_boltz_probe_pipes(void *cuda_stream, double *rates_out);
+
+/*
+ * The FP32 spreading kernels' grid coordinates, for testing them: for each of the n velocities
+ * v_dev[i] (device, FP32) of one mapped axis, the grid coordinate x = n_grid z / (2 pi) of
+ * z = arccos(xi(v)) (Section 2.1 maps: map_log 0 algebraic r = 1, 1 logarithmic r = 0, scale S)
+ * as the kernels form it: an integer cell cell_dev[i] and a fraction frac_dev[i] in [0, 1)
+ * (x = cell + frac), and m2_dev[i] = mu(xi(v))^-2 in FP32.  cell_dev, frac_dev, m2_dev: device
+ * arrays of n doubles.  n_grid: the (even) periodic grid size.  Asynchronous on cuda_stream.
+ * PG_OK, PG_ERR_ARG or PG_ERR_CUDA.
+ */
+int pg_boltz_grid_coords_f32(const float *v_dev, long long n, double S, int map_log, int n_grid, double *cell_dev,
+                             double *frac_dev, double *m2_dev, void *cuda_stream);
+
+/*
  * Size of the library-owned static device array used by pg_boltz_project_noalloc
  * (4 MiB of doubles, held on every GPU that loads the library until process exit).
  */
@@ -305,18 +327,18 @@ int pg_boltz_probe_shared_atomics(void *cuda_stream, double *rate_out);
  * bindings that can only pass pointers they already hold -- and therefore cannot create
  * a plan (plans allocate their tables and workspace).
  *
- * Computes f~_k = (f, That_k) for 0 <= k_l <= N (Eq. MultiD_spectral_coef) by Chebyshev-Gauss
- * quadrature with Mp nodes per axis, exactly as pg_boltz_project on a plan with the same
- * d, N, S, map and proj_nodes = Mp (nodes from pg_boltz_project_nodes).
+ * Computes the same coefficients as pg_boltz_project on a plan with the same d, N, S, map
+ * and proj_nodes = Mp (nodes from pg_boltz_project_nodes), up to rounding.
  *   d: 2 or 3; N >= 2; S > 0; map_log: 0 algebraic (r = 1), 1 logarithmic (r = 0); Mp >= 1.
  *   fvals_dev: device array of Mp^d doubles (f at the tensor grid of the nodes, C order).
  *   ftilde_dev: device array of (N+1)^d doubles, written.
  *   cuda_stream: a cudaStream_t (NULL = legacy default stream); the call is asynchronous.
  * Scratch: (N+1) Mp + (N+1) Mp^(d-1) [+ (N+1)^2 Mp when d = 3] doubles of the static array of
  * PG_BOLTZ_NOALLOC_SCRATCH_BYTES; larger requests return PG_ERR_ARG (see pg_boltz_last_error).
- * It calls no cudaMalloc, cudaFree or other allocating routine.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress, with that device current) and
- * caches it; make that first call before any stream capture.  All calls share the array,
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  Every call looks up the
+ * array's device address with cudaGetSymbolAddress on the current device (no cache, so a
+ * device reset or a change of context needs no special care); the first call in a context may
+ * load the library's device code there, so make it before any stream capture.  All calls share the array,
  * which keeps the last call's contents (every value a call reads it has written itself, so
  * nothing needs clearing); calls that overlap on the GPU (different streams, or another
  * host thread) race on it and must be serialised by the caller.

@@ -26,7 +26,8 @@ EXPORTS = (
     "pg_boltz_stage_times", "pg_boltz_project_noalloc", "pg_boltz_probe_shared_atomics",
     "pg_boltz_plan_batched", "pg_boltz_plan_batched_ex", "pg_boltz_collide_batched", "pg_boltz_batched_offsets",
     "pg_boltz_batched_use_graph", "pg_boltz_rk4", "pg_boltz_conservation", "pg_boltz_evaluate",
-    "pg_boltz_adaptive_scale", "pg_boltz_batched_autotune", "pg_boltz_kernel_poly",
+    "pg_boltz_adaptive_scale", "pg_boltz_batched_autotune", "pg_boltz_kernel_poly", "pg_boltz_probe_pipes",
+    "pg_boltz_grid_coords_f32",
 )
 
 
@@ -110,6 +111,11 @@ def lib():
     L.pg_boltz_rk4.restype = ctypes.c_int
     L.pg_boltz_probe_shared_atomics.argtypes = [vp, dp]
     L.pg_boltz_probe_shared_atomics.restype = ctypes.c_int
+    L.pg_boltz_probe_pipes.argtypes = [vp, dp]
+    L.pg_boltz_probe_pipes.restype = ctypes.c_int
+    L.pg_boltz_grid_coords_f32.argtypes = [vp, ctypes.c_longlong, ctypes.c_double, ctypes.c_int, ctypes.c_int, vp, vp,
+                                           vp, vp]
+    L.pg_boltz_grid_coords_f32.restype = ctypes.c_int
     L.pg_boltz_set_timing.argtypes = [vp, ctypes.c_int]
     L.pg_boltz_stage_times.argtypes = [vp, dp]
     for name in ("pg_boltz_set_timing", "pg_boltz_stage_times", "pg_boltz_set_stream", "pg_boltz_collide", "pg_boltz_moments", "pg_boltz_project_nodes",
@@ -142,6 +148,24 @@ def probe_shared_atomics(stream=None) -> float:
     raw = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     _check(lib().pg_boltz_probe_shared_atomics(ctypes.c_void_p(raw), ctypes.byref(out)))
     return out.value
+
+
+def probe_pipes(stream=None):
+    """Measured (FP32 FMA/s, FP64 FMA/s, conflict-free int32 shared atomics/s) of the current GPU."""
+    out = (ctypes.c_double * 3)()
+    raw = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(lib().pg_boltz_probe_pipes(ctypes.c_void_p(raw), out))
+    return tuple(out)
+
+
+def grid_coords_f32(v, S: float, map_log: bool, n_grid: int, cell_out, frac_out, m2_out, stream=None):
+    """FP32 spreading grid coordinates (cell, fraction in [0, 1)) and mu^-2 of float32 CUDA tensor v."""
+    if str(v.dtype) != "torch.float32" or not v.is_cuda or not v.is_contiguous():
+        raise ValueError("v must be a contiguous float32 CUDA tensor")
+    raw = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(lib().pg_boltz_grid_coords_f32(ctypes.c_void_p(v.data_ptr()), v.numel(), float(S), int(bool(map_log)),
+                                          int(n_grid), ctypes.c_void_p(_ptr(cell_out)), ctypes.c_void_p(_ptr(frac_out)),
+                                          ctypes.c_void_p(_ptr(m2_out)), ctypes.c_void_p(raw)))
 
 
 def adaptive_scale(N: int, L: float, map_log: bool = False) -> float:

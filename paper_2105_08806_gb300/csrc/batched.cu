@@ -44,6 +44,7 @@ struct CellDesc {
     int sig_off;         // sphere points (M x d) and weights (M)
     int chunk;           // node pairs per work item
     int item0;           // first work item of the cell
+    double corr;         // FP32 plans: exact / FP32 constant factors of the strengths (1 for FP64)
 };
 
 struct BatchArgs {
@@ -65,6 +66,7 @@ struct BatchArgs {
     double *scratch;
     const double *v64;
     const float *v32;
+    const float *v32lo;  // v - (double)v32 (FP32 nodes' rounding)
     const double *scale_a;
     const double *inv_mu2;
     const double *R;
@@ -192,8 +194,13 @@ __global__ void __launch_bounds__(kPrepThreads) k_batch_prep(const __grid_consta
     __syncthreads();
     // 2. loss sums and the strength bound
     const PT *vn = nullptr;
-    if constexpr (sizeof(PT) == 4) vn = b.v32 + cd.node_off;
-    else vn = b.v64 + cd.node_off;
+    const float *vlo = nullptr;  // FP32 nodes' rounding, added back to the node differences
+    if constexpr (sizeof(PT) == 4) {
+        vn = b.v32 + cd.node_off;
+        vlo = b.v32lo + cd.node_off;
+    } else {
+        vn = b.v64 + cd.node_off;
+    }
     const double *im = b.inv_mu2 + cd.node_off;
     const double Bw = b.Bconst * cd.Wsig;
     const PT S = PT(cd.S), invS = PT(1) / S, gam = PT(cd.gamma);
@@ -204,20 +211,24 @@ __global__ void __launch_bounds__(kPrepThreads) k_batch_prep(const __grid_consta
             idx[l] = t % N;
             t /= N;
         }
-        PT vi[3];
+        PT vi[3], vil[3] = {PT(0), PT(0), PT(0)};
         for (int l = 0; l < 3; ++l) vi[l] = (l < d) ? vn[idx[l]] : PT(0);
+        if (vlo)
+            for (int l = 0; l < d; ++l) vil[l] = PT(vlo[idx[l]]);
         double L = 0.0, U = 0.0;
         for (int j0 = 0; j0 < nnode; j0 += 64) {
-            PT Lp = PT(0), Up = PT(0);  // partial sums of 64 terms, then FP64
+            PT Up = PT(0);  // bound: partial sums of 64 terms, then FP64
             const int j1 = min(j0 + 64, nnode);
             for (int j = j0; j < j1; ++j) {
                 int u = j;
                 PT g2 = PT(0), mu = PT(1);
                 PT vj[3];
                 for (int l = d - 1; l >= 0; --l) {
-                    vj[l] = vn[u % N];
+                    const int nj = u % N;
+                    vj[l] = vn[nj];
                     u /= N;
-                    const PT dl = vi[l] - vj[l];
+                    PT dl = vi[l] - vj[l];
+                    if (vlo) dl += vil[l] - PT(vlo[nj]);
                     g2 += dl * dl;
                 }
                 const PT g = sqrt(g2);
@@ -229,7 +240,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_batch_prep(const __grid_consta
                 default: B = (g2 > PT(0)) ? pow(g, gam) : PT(0); break;
                 }
                 const PT aj = PT(a[j]);
-                Lp = fma(aj, B, Lp);  // as the single-plan loss kernel
+                L = fma(double(B), a[j], L);  // as the single-plan loss kernel
                 for (int l = 0; l < d; ++l) {
                     const PT R_ = fabs(PT(0.5) * (vi[l] + vj[l])) + PT(0.5) * g;
                     mu *= (b.r == 1) ? (S * S + R_ * R_) * invS : S * cosh(R_ * invS);
@@ -238,7 +249,6 @@ __global__ void __launch_bounds__(kPrepThreads) k_batch_prep(const __grid_consta
                 Up += pb;
                 if (screen && pb > PT(0)) atomicAdd(&s_hist[screen_bin(fabs(a[i]) * Bw * (double)pb)], 1u);
             }
-            L += (double)Lp;
             U += (double)Up;
         }
         double scl = 1.0;
@@ -286,6 +296,7 @@ __device__ __forceinline__ void cell_args(const BatchArgs &b, const CellDesc &cd
     sa.beta = b.beta;
     sa.grid_scale = cd.n / (2.0 * 3.14159265358979323846);
     sa.vnode = f32 ? (const void *)(b.v32 + cd.node_off) : (const void *)(b.v64 + cd.node_off);
+    sa.vnode_lo = f32 ? b.v32lo + cd.node_off : nullptr;
     sa.a = f32 ? (const void *)(b.a32 + cd.a_off) : (const void *)(b.a64 + cd.a_off);
     sa.sig = f32 ? (const void *)(b.sig32 + cd.sig_off * b.d) : (const void *)(b.sig64 + cd.sig_off * b.d);
     sa.wsig = f32 ? (const void *)(b.wsig32 + cd.sig_off) : (const void *)(b.wsig64 + cd.sig_off);
@@ -300,6 +311,7 @@ __device__ __forceinline__ void cell_args(const BatchArgs &b, const CellDesc &cd
     sa.cpad = tile_col_pad(b.w);
     sa.ncol = cd.nf + 2 * sa.cpad;
     sa.kpoly = b.kpoly;
+    fill_spread_consts(sa);
 }
 
 template <typename T>
@@ -331,7 +343,7 @@ __global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __gr
     __shared__ CellDesc s_cd;
     constexpr bool F32 = (sizeof(T) == 4);
     int cur = -1, ncell = 0, plane = 0, Eg = 0, shift = 0;
-    T sc = T(0), tau = T(0);
+    T sc = T(0), tau = T(0), floor_q = T(0);
     // the current cell's spreading arguments live in shared memory: kept in registers they cost
     // 30-odd registers per thread (fewer resident warps, or spills under a 1024-thread bound)
     __shared__ SpreadArgs s_sa;
@@ -365,6 +377,9 @@ __global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __gr
             shift = Eg - Et;
             sc = F32 ? T(ldexp(1.0, Et)) : T(1);
             tau = T(b.Tcell[cell]);
+            // negligible pairs: FP32 points below 0.1 tile unit add exactly zero; FP64 pairs whose
+            // summed bounds stay below 2^-64 B
+            floor_q = F32 ? T(spread_detail::kNegligibleF32) : T(ldexp(Bc, -64) * sa.cd.wmax / (double)s_cd.pairs);
             for (int e = threadIdx.x; e < ncell; e += blockDim.x) {
                 if constexpr (F32) {
                     lo[e] = 0;
@@ -378,18 +393,13 @@ __global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __gr
         // the item's node pairs; lanes of a warp take pairs nwarp apart
         const long long p0 = (long long)(item - s_cd.item0) * s_cd.chunk;
         const long long p1 = min(p0 + (long long)s_cd.chunk, s_cd.pairs);
-        for (long long pr = p0 + (long long)lane * nwarp + warp; pr < p1; pr += blockDim.x) {
-            PairData<T, D> P;
-            if (!load_pair<T, D>(sa, pr, P)) continue;
-            if (tau > T(0) && pair_bound<T, D>(sa, P) < tau) continue;
-            P.base *= P.mult;
-            if constexpr (F32) {
-                const SplitTile tile{lo, carry};
-                spread_pair<T, D, W>(sa, P, sc, tile, 0, s_cd.nf, plane);
-            } else {
-                spread_pair<T, D, W>(sa, P, sc, DoubleTile{dv}, 0, s_cd.nf, plane);
-            }
-        }
+        const long long first = p0 + (long long)lane * nwarp + warp;
+        if constexpr (F32)
+            spread_pairs<T, D, W, SplitTile, false>(sa, first, p1, blockDim.x, sc, tau, floor_q, SplitTile{lo, carry}, 0,
+                                                     s_cd.nf, plane);
+        else
+            spread_pairs<T, D, W, DoubleTile, false>(sa, first, p1, blockDim.x, sc, tau, floor_q, DoubleTile{dv}, 0,
+                                                      s_cd.nf, plane);
         __syncthreads();
     }
     if (cur >= 0) batch_flush<F32, D>(lo, carry, dv, ncell, s_cd.nf, sa.ncol, sa.cpad, s_cd.n, sa.grid, shift, Eg);
@@ -404,7 +414,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_batch_final(const __grid_const
     double *s1 = b.scratch + cd.s_off, *s2 = s1 + cd.s_len, *s3 = s2 + cd.s_len, *s4 = s3 + cd.s_len;
     const double *Dm = b.D + cd.D_off;
     const double *E = b.E + cd.R_off;
-    const double unit = ldexp(1.0, -global_exponent(b.Bcell[c]));
+    const double unit = ldexp(cd.corr, -global_exponent(b.Bcell[c]));
     Dims3 gd = dims3(d, nf, nf, nf);
     const int ax0 = 3 - d;
     block_pass_fixed(b.grid + cd.grid_off, gd, ax0, Dm, N + 1, unit, s1);
@@ -696,6 +706,9 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
         cd.sig_off = sig_key[M];
         cd.Wsig = 0.0;
         for (int m = 0; m < M; ++m) cd.Wsig += wsig64[cd.sig_off + m];
+        cd.corr = (B->prec == PG_PREC_FP32)
+                      ? pgb::fp32_strength_correction(1.0 / (d == 2 ? 2.0 * kPi : 4.0 * kPi), wsig64[cd.sig_off], Ss[c], d)
+                      : 1.0;
         const long long modes = (long long)ipow(N + 1, d);
         cd.f_off = f_off;
         B->offsets[c] = f_off;
@@ -722,6 +735,8 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
     B->nitems = (int)item_cell.size();
     B->grid_cells = grid_off;
     std::vector<float> v32(v64.begin(), v64.end()), sig32(sig64.begin(), sig64.end()), wsig32(wsig64.begin(), wsig64.end());
+    std::vector<float> v32lo(v64.size());
+    for (size_t k = 0; k < v64.size(); ++k) v32lo[k] = (float)(v64[k] - (double)v32[k]);
 
     pgb::BatchArgs &a = B->args;
     a.d = d;
@@ -736,13 +751,14 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
     int *d_items = nullptr;
     double *d_v64 = nullptr, *d_sa = nullptr, *d_im = nullptr, *d_R = nullptr, *d_E = nullptr, *d_D = nullptr,
            *d_s64 = nullptr, *d_w64 = nullptr, *d_kp = nullptr;
-    float *d_v32 = nullptr, *d_s32 = nullptr, *d_w32 = nullptr;
+    float *d_v32 = nullptr, *d_v32lo = nullptr, *d_s32 = nullptr, *d_w32 = nullptr;
     void *counter_grid = nullptr;
     std::vector<double> kpoly(pgb::kPolyCoefF64, 0.0);
     kernel_poly(B->w, B->beta, kpoly.data());
     // each failing call has recorded its error for pg_boltz_last_error
     if (upload(p, &d_cells, cells) || upload(p, &d_kp, kpoly) || upload(p, &d_items, item_cell) ||
-        upload(p, &d_v64, v64) || upload(p, &d_v32, v32) || upload(p, &d_sa, scale_a) || upload(p, &d_im, inv_mu2) ||
+        upload(p, &d_v64, v64) || upload(p, &d_v32, v32) || upload(p, &d_v32lo, v32lo) || upload(p, &d_sa, scale_a) ||
+        upload(p, &d_im, inv_mu2) ||
         upload(p, &d_R, R) || upload(p, &d_E, E) || upload(p, &d_D, D) || upload(p, &d_s64, sig64) ||
         upload(p, &d_s32, sig32) || upload(p, &d_w64, wsig64) || upload(p, &d_w32, wsig32) ||
         dev_alloc(p, (void **)&a.a64, a_off * 8) || dev_alloc(p, (void **)&a.a32, a_off * 4) ||
@@ -758,6 +774,7 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
     a.grid = reinterpret_cast<unsigned long long *>(static_cast<char *>(counter_grid) + 256);
     a.v64 = d_v64;
     a.v32 = d_v32;
+    a.v32lo = d_v32lo;
     a.scale_a = d_sa;
     a.inv_mu2 = d_im;
     a.R = d_R;

@@ -117,6 +117,8 @@ struct pg_boltz_plan_s {
     double *inv_mu2 = nullptr; // N: 1/mu_i^2
     double *v64 = nullptr;     // N node velocities
     float *v32 = nullptr;
+    float *v32lo = nullptr;  // v - (double)v32: the FP32 nodes' rounding
+    double grid_scale_corr = 1.0;  // FP32 plans: exact / FP32 constant factors of the strengths
     double *sig64 = nullptr, *wsig64 = nullptr;  // M x d, M
     float *sig32 = nullptr, *wsig32 = nullptr;
     // workspace

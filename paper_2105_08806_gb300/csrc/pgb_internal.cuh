@@ -26,6 +26,23 @@ struct Angular {
     double c[kMaxAngular];
 };
 
+// Loop-invariant constants of the spreading kernels in their arithmetic type, filled once on the
+// host (or by the batched kernel's cell switch) so the point loops convert nothing from double.
+template <typename T>
+struct TypedConsts {
+    T S, invS, SS;      // map scale, 1/S, S^2
+    T gs;               // grid_scale
+    T Bconst, gamma;    // kernel constant and exponent
+    T Wang;             // Wsig * angmax (pair bound factor)
+    T wmax;             // wmax_frac
+    T bl;               // beta log2(e): ES kernel values as powers of two
+    T ang_even[kMaxAngular / 2];
+    // FP32 point coordinates without systematic offsets or scale errors: a grid coordinate is
+    // x = xq -+ atan(v/S) gs (r = 1) or 2 atan(exp(-v/S)) gs (r = 0) with xq = n/4 exact and the
+    // products by 1/S and gs carried in two terms (hi + lo); zero in TypedConsts<double>
+    T invS_lo, gs_lo, xq;
+};
+
 struct SpreadArgs {
     int d, N, M, r;
     int nnode;            // N^d interior nodes
@@ -38,6 +55,8 @@ struct SpreadArgs {
     double beta;          // exponential-of-semicircle shape
     double grid_scale;    // n / (2 pi): angle -> grid coordinate
     const void *vnode;    // N node velocities (same on every axis)
+    const float *vnode_lo;  // FP32 plans: v - (double)vnode, so that hi + lo carries the node exactly
+                            // to about 2^-48 (nullptr for FP64 plans)
     const void *a;        // nnode values a_i = W_i g_i
     const void *sig;      // M x d sphere points
     const void *wsig;     // M sphere weights
@@ -61,17 +80,53 @@ struct SpreadArgs {
     // kpoly[a P + k] (device, kPolyCoefF64 doubles) holds the (P+1)/2 coefficients of E_a, then
     // the P/2 of O_a, lowest power first
     const double *kpoly;
+    TypedConsts<float> cf;   // the double fields above as float (FP32 kernels)
+    TypedConsts<double> cd;  // ... and as double (FP64 kernels)
 };
+
+// Fill a.cf and a.cd from the double fields (call after setting S, grid_scale, Bconst, gamma,
+// Wsig, angmax, wmax_frac, beta and ang_even).
+template <typename T>
+__host__ __device__ inline void fill_typed_consts(const SpreadArgs &a, TypedConsts<T> &c)
+{
+    c.S = T(a.S);
+    c.invS = T(1.0 / a.S);
+    c.SS = T(a.S * a.S);
+    c.gs = T(a.grid_scale);
+    c.Bconst = T(a.Bconst);
+    c.gamma = T(a.gamma);
+    c.Wang = T(a.Wsig * a.angmax);
+    c.wmax = T(a.wmax_frac);
+    c.bl = T(a.beta * 1.4426950408889634);
+    for (int k = 0; k < kMaxAngular / 2; ++k) c.ang_even[k] = T(k < a.nang_even ? a.ang_even[k] : 0.0);
+    c.invS_lo = T(1.0 / a.S - double(c.invS));
+    c.gs_lo = T(a.grid_scale - double(c.gs));
+    c.xq = T(0.25 * a.n);
+}
+__host__ __device__ inline void fill_spread_consts(SpreadArgs &a)
+{
+    fill_typed_consts<float>(a, a.cf);
+    fill_typed_consts<double>(a, a.cd);
+}
+template <typename T>
+__device__ __forceinline__ const TypedConsts<T> &kconst(const SpreadArgs &a)
+{
+    if constexpr (sizeof(T) == 4) return a.cf;
+    else return a.cd;
+}
 
 // Node pairs the spreading kernels walk: each unordered pair {i, j} once (the two orders add the
 // same points with the same strength), nnode (nnode + 1) / 2 in all.
 __host__ __device__ inline long long unordered_pairs(long long nnode) { return nnode * (nnode + 1) / 2; }
 
+// Values per queued point of the slabbed spreading kernels: FP32 points keep each coordinate as
+// a cell and a fraction (2d + 1 floats with the strength), FP64 points d + 1 doubles.
+__host__ __device__ inline int spread_queue_values(int d, bool f32) { return f32 ? 2 * d + 1 : d + 1; }
 // Shared memory of the warp point queues of a slabbed spreading block of `threads` threads:
-// 32 points per warp, d coordinates and a strength of `elem` bytes each.
-__host__ __device__ inline size_t spread_queue_bytes(int threads, int d, size_t elem)
+// 32 points per warp.
+__host__ __device__ inline size_t spread_queue_bytes(int threads, int d, bool f32)
 {
-    return (size_t)(threads / 32) * 32 * (d + 1) * elem;
+    return (size_t)(threads / 32) * 32 * spread_queue_values(d, f32) * (f32 ? 4 : 8);
 }
 
 // Padding columns of the block tiles' last axis for kernel width w: the unfolded support of a point
@@ -132,11 +187,13 @@ cudaError_t launch_recon_last(const double *in, Dims3 in_dims, const double *A, 
 // A_ij = (1/Wsig) sum_m w_m b(cos theta_ijm) for an angular kernel (ang.n > 0; the sum over the
 // sphere set then runs per pair), 1 otherwise (Bw = Bconst Wsig);
 // also ub_i = |a_i| Bw angmax sum_j |a_j| B_ij prod_l mu^-2(|c_l| + rad), an upper bound of the
-// spreading strengths of the pairs (i, .).  FP32 pair terms carry a relative error near 1e-7,
-// well inside the FP32 path's tolerance; the bound gets a 1e-5 margin in k_bound_reduce.
+// spreading strengths of the pairs (i, .).  FP32 pair terms (node differences with the nodes'
+// rounding vnode32_lo added back, summed in FP64) carry a relative error near 1e-7 that differs
+// from pair to pair; the bound gets a 1e-5 margin in k_bound_reduce.
 // vnode32 != nullptr selects FP32 pair terms (the FP32 path).
 // hist != nullptr: also count every pair bound |a_i| Bw |a_j| B_ij prod mu^-2 into the screening histogram.
-cudaError_t launch_loss(const double *a, const double *vnode, const float *vnode32, int N, int d, int M,
+cudaError_t launch_loss(const double *a, const double *vnode, const float *vnode32, const float *vnode32_lo, int N,
+                        int d, int M,
                         const double *sig, const double *wsig, const float *sig32, const float *wsig32,
                         const Angular &ang, double angmax, double Wsig, double gamma,
                         int fast_gamma, double Bw, const double *inv_mu2, double S, int r,
@@ -153,9 +210,18 @@ __host__ __device__ inline int screen_bin(double u)
 // (an upper bound of the total strength of the pairs below tau), else *tau = 0.
 cudaError_t launch_bound_reduce(const double *ub, int n, const unsigned long long *hist, double eps, double *B,
                                 double *tau, cudaStream_t s);
-// First transform pass reading the int64 fixed-point grid (units 2^-Eg, Eg from *B).
+// First transform pass reading the int64 fixed-point grid (units 2^-Eg, Eg from *B), times scale.
 cudaError_t launch_axis_pass_fixed(const unsigned long long *in, Dims3 in_dims, int ax, const double *A,
-                                   int m, const double *B, double *out, cudaStream_t s);
+                                   int m, const double *B, double scale, double *out, cudaStream_t s);
+// Exact / FP32 value of the constant factors of an FP32 point strength: Bconst (the kernel's
+// constant), the common sphere weight w and 1/S per axis enter every strength as rounded FP32
+// constants, a common relative error that the transform of the FP32 grid divides out in FP64.
+inline double fp32_strength_correction(double Bconst, double w, double S, int d)
+{
+    double c = (Bconst / (double)(float)Bconst) * (w / (double)(float)w);
+    for (int l = 0; l < d; ++l) c *= (1.0 / S) / (double)(float)(1.0 / S);
+    return c;
+}
 // Final pass along axis 2: Qp = D . G, Qm = E . H, Q = Qp - Qm (also copied to Qcopy).
 cudaError_t launch_final(const double *G, Dims3 g_dims, const double *D, const double *H,
                          Dims3 h_dims, const double *E, int m, double *Q, double *Qplus,

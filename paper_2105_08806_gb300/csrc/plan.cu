@@ -57,7 +57,8 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
 
     // ---- node tables and the cosine transform with deconvolution
     NodeTables nt = node_tables(N, p->S, p->r);
-    std::vector<float> vf(nt.v.begin(), nt.v.end());
+    std::vector<float> vf(nt.v.begin(), nt.v.end()), vflo(nt.v.size());
+    for (size_t k = 0; k < vflo.size(); ++k) vflo[k] = (float)(nt.v[k] - (double)vf[k]);
     std::vector<double> D = transform_matrix(N, p->n, p->w, p->beta);
     // ---- projection (Chebyshev-Gauss): P[k][p] = (pi/Mp) mu_p^-4 T_k(xi_p) / sqrt(c_k)
     const int Mp = p->Mp;
@@ -81,7 +82,7 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
     if ((rc = upload(p, &p->R, nt.R)) || (rc = upload(p, &p->E, nt.E)) || (rc = upload(p, &p->Dm, D)) ||
         (rc = upload(p, &p->Pm, P)) || (rc = upload(p, &p->scale_a, nt.scale_a)) ||
         (rc = upload(p, &p->inv_mu2, nt.inv_mu2)) || (rc = upload(p, &p->v64, nt.v)) ||
-        (rc = upload(p, &p->v32, vf)) || (rc = upload(p, &p->sig64, sp)) ||
+        (rc = upload(p, &p->v32, vf)) || (rc = upload(p, &p->v32lo, vflo)) || (rc = upload(p, &p->sig64, sp)) ||
         (rc = upload(p, &p->wsig64, sw)) || (rc = upload(p, &p->sig32, spf)) || (rc = upload(p, &p->wsig32, swf)))
         return rc;
 
@@ -125,7 +126,7 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
         // slabbed grid: the warps' point queues (one block per SM, max_threads threads unless
         // set) share the block's shared memory with the slab
         const int thr = (o.spread_threads > 0) ? o.spread_threads : max_threads;
-        qbytes = pgb::spread_queue_bytes(thr, d, f32 ? 4 : 8);
+        qbytes = pgb::spread_queue_bytes(thr, d, f32);
         rows_fit = (max_smem > qbytes) ? (int)std::min<size_t>(p->nf, (max_smem - qbytes) / (plane * elem)) : 0;
     }
     if (rows_fit < 1) return set_error(PG_ERR_ARG, "folded grid plane of %zu cells does not fit shared memory", plane);
@@ -150,7 +151,7 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
     if (p->nslab > 1 && o.spread_threads <= 0) p->spread_threads = max_threads;  // the queues were sized for it
     if (p->spread_threads % 32 || p->spread_threads > max_threads)
         return set_error(PG_ERR_ARG, "spread_threads must be a multiple of 32 and <= %d", max_threads);
-    if (p->nslab > 1 && pgb::spread_queue_bytes(p->spread_threads, d, f32 ? 4 : 8) > qbytes)
+    if (p->nslab > 1 && pgb::spread_queue_bytes(p->spread_threads, d, f32) > qbytes)
         return set_error(PG_ERR_STATE, "internal: point queues larger than reserved");
     per_sm = std::min(per_sm, prop.maxThreadsPerMultiProcessor / p->spread_threads);
     if (o.spread_blocks_per_sm > 0) per_sm = std::min(per_sm, o.spread_blocks_per_sm);
@@ -194,11 +195,14 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
     ka.beta = p->beta;
     ka.grid_scale = p->n / (2.0 * kPi);
     ka.vnode = f32 ? (const void *)p->v32 : (const void *)p->v64;
+    ka.vnode_lo = f32 ? p->v32lo : nullptr;
     ka.a = f32 ? (const void *)p->a32 : (const void *)p->a64;
     ka.sig = f32 ? (const void *)p->sig32 : (const void *)p->sig64;
     ka.wsig = f32 ? (const void *)p->wsig32 : (const void *)p->wsig64;
     ka.Wsig = p->Wsig;
     ka.wmax_frac = *std::max_element(sw.begin(), sw.end()) / p->Wsig;
+    // FP32 strengths carry Bconst, the (common) sphere weight and 1/S as rounded FP32 constants
+    p->grid_scale_corr = f32 ? pgb::fp32_strength_correction(p->Bconst, sw[0], p->S, d) : 1.0;
     ka.bound = p->bound;
     ka.tau = p->tau;
     ka.grid = p->grid;
@@ -211,6 +215,7 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
     for (int k = 0; k < ka.nang_even; ++k) ka.ang_even[k] = p->ang.c[2 * k];
     ka.angmax = p->angmax;
     ka.kpoly = p->kpoly;
+    pgb::fill_spread_consts(ka);
     return PG_OK;
 }
 
@@ -380,7 +385,7 @@ PG_API int pg_boltz_collide(pg_boltz_plan_t *p, const double *f_dev, double *Q_d
                          "memset grid")))
         return rc;
     ++launches;
-    if ((rc = cuda_check(pgb::launch_loss(p->a64, p->v64, f32 ? p->v32 : nullptr, N, d, p->M, p->sig64, p->wsig64,
+    if ((rc = cuda_check(pgb::launch_loss(p->a64, p->v64, f32 ? p->v32 : nullptr, p->v32lo, N, d, p->M, p->sig64, p->wsig64,
                                           p->sig32, p->wsig32, p->ang, p->angmax, p->Wsig, p->gamma, p->fast_gamma,
                                           p->Bconst * p->Wsig, p->inv_mu2, p->S, p->r, p->h, p->ub,
                                           p->screen_eps > 0.0 ? p->hist : nullptr, p->stream),
@@ -405,7 +410,8 @@ PG_API int pg_boltz_collide(pg_boltz_plan_t *p, const double *f_dev, double *Q_d
     //    forward Chebyshev transform of the loss
     pgb::Dims3 gd = dims_of(d, p->nf, p->nf, p->nf);
     const int ax0 = 3 - d;
-    if ((rc = cuda_check(pgb::launch_axis_pass_fixed(p->grid, gd, ax0, p->Dm, N + 1, p->bound, p->tA, p->stream),
+    if ((rc = cuda_check(pgb::launch_axis_pass_fixed(p->grid, gd, ax0, p->Dm, N + 1, p->bound, p->grid_scale_corr,
+                                                     p->tA, p->stream),
                          "transform pass")))
         return rc;
     ++launches;

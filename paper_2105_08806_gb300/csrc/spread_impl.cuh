@@ -28,15 +28,24 @@
 //  - FP64 kernel: each block adds into a private FP64 copy of its slab of the grid in shared
 //    memory; at the end each cell's partial sum is rounded to the grid unit (relative error
 //    2^-61 B) and added to the global grid.
-//  - FP32 kernel: the private copy holds one signed 32-bit fixed-point word per cell in units of
-//    2^-Et, Et = Eg - kTileBits, plus per-cell carry counters in a per-block global array
-//    (SplitTile): a contribution goes to its word with one native 32-bit shared atomic, and only
-//    an addition that wraps the word's signed range (seen from the returned old value) adds +-1
-//    to the cell's carry counter (units of 2^32).  (Floating-point shared atomics are
-//    compare-and-swap loops and their rounding limits FP32 accuracy; 64-bit integer shared
-//    atomics are several times slower than 32-bit ones.)  At the end each block adds
-//    word + carry 2^32 (scaled by 2^kTileBits) to the global grid.  Each contribution is rounded
-//    once, to the tile unit; all later additions are exact.
+//  - FP32 kernel: the private copy holds one signed 32-bit word per cell in units of 2^-Et,
+//    Et = Eg - kTileBits, plus per-cell carry counters in a per-block global array (SplitTile):
+//    the cell's value is word + 2^32 carry.  A contribution goes to its word with one native 32-bit
+//    shared atomic, and only an addition that overflows the word's signed range (seen from the
+//    returned old value) moves the cell's carry counter.  (Floating-point shared atomics are
+//    compare-and-swap loops and their rounding limits FP32 accuracy; 64-bit integer shared atomics
+//    are several times slower than 32-bit ones.)  Points below 2^29 tile units -- nearly all of
+//    them -- form their contributions in integers: the row factor 4 q psi_a (psi_b) and the column
+//    factor 2^30 psi_c are rounded once per row and column, and a contribution is the rounded high
+//    word of their 64-bit product (one integer multiply-add).  At the end each block adds
+//    word + 2^32 carry (scaled by 2^kTileBits) to the global grid.  Each contribution is rounded
+//    to the tile unit (at most about one unit); all later additions are exact.
+//
+// Negligible pairs: a pair whose strength bound keeps every one of its points below 0.1 tile unit
+// adds exactly zero (every contribution rounds to zero), so the FP32 kernels skip it; FP64
+// kernels skip pairs whose summed bounds stay below 2^-64 B.  Each lane searches ahead for its
+// next pair that is not negligible, so that the lanes of a warp spread real pairs together (with
+// the node sets of the workloads here, 25-75% of all pairs lie in the tails of f and are skipped).
 #pragma once
 
 #include <climits>
@@ -86,11 +95,8 @@ __device__ __forceinline__ int fold_cell(int u, int n, bool simple)
     return fold_index(u, n);
 }
 
-// The w kernel weights psi(x_u - z) of one axis, u = s..s+w-1, in units where one grid cell
-// is 1 and x = z n / (2 pi): psi = exp(beta (sqrt(1 - t^2) - 1)), t = (u - x) 2/w.  Returns
-// the first unfolded index s.
-template <int W>
-__device__ __forceinline__ int kernel_weights_f32(const SpreadArgs &p, float x, float *wt);
+// Kernel weights psi(x_u - z) of one axis, u = s..s+w-1, in units where one grid cell is 1 and
+// x = z n / (2 pi): psi = exp(beta (sqrt(1 - t^2) - 1)), t = (u - x) 2/w.
 
 // FP64: psi of tap a is a polynomial (kernel_poly_terms(w) terms) in the point's offset
 // y = 2 (s - x) + w - 1 in (-1, 1] (t = (y + 1 + 2a - w)/w), fitted on the host.  Taps a and
@@ -137,18 +143,11 @@ __device__ __forceinline__ int kernel_weights_f64(double x, double *wt)
     return s;
 }
 
-template <typename T, int W>
-__device__ __forceinline__ int kernel_weights(const SpreadArgs &p, T x, T *wt)
+// FP64 weights and the folded cells fold(s + a) of one axis.
+template <int W>
+__device__ __forceinline__ void axis_weights_f64(const SpreadArgs &p, double x, double *wt, int *idx)
 {
-    if constexpr (sizeof(T) == 4) return kernel_weights_f32<W>(p, x, wt);
-    else return kernel_weights_f64<W>(x, wt);
-}
-
-// The weights and the folded cells fold(s + a) of one axis.
-template <typename T, int W>
-__device__ __forceinline__ void axis_weights(const SpreadArgs &p, T x, T *wt, int *idx)
-{
-    const int s = kernel_weights<T, W>(p, x, wt);
+    const int s = kernel_weights_f64<W>(x, wt);
     const bool simple = p.simple_fold != 0;
 #pragma unroll
     for (int a = 0; a < W; ++a) idx[a] = fold_cell(s + a, p.n, simple);
@@ -174,62 +173,132 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
-// atan(t) for t >= 0: t P(t^2) on [0, 1] and pi/2 - atan(1/t) above.  P is a degree-8
-// polynomial in t^2 fitted to atan(t)/t on [0, 1] by iteratively reweighted least squares
-// (towards the minimax error of t P(t^2)); its error is below 1e-7 when evaluated in FP32.
-__device__ __forceinline__ float atan_pos_f32(float t)
+// atan(u) - u for |u| <= 1 as u^3 R(u^2): R is a degree-9 polynomial in u^2 fitted by
+// fit_atan_f32.py (iteratively reweighted least squares towards the minimax error of atan; the
+// fit's error is 1.7e-10, and evaluated in FP32 the correction carries at most 3e-8).  The
+// leading term u stays exact, so atan(u) is carried as the two terms u + correction.
+__device__ __forceinline__ float atan_correction_f32(float u)
 {
-    const bool inv = t > 1.0f;
-    const float u = inv ? rcp_approx(t) : t;
-    const float x = u * u;
-    float p = 0.002455897797786189f;
-    p = fmaf(p, x, -0.014397678937342222f);
-    p = fmaf(p, x, 0.03977441675320232f);
-    p = fmaf(p, x, -0.07234180246738538f);
-    p = fmaf(p, x, 0.10498555283788273f);
-    p = fmaf(p, x, -0.1416109770841035f);
-    p = fmaf(p, x, 0.19985882274088168f);
-    p = fmaf(p, x, -0.33332594819936656f);
-    p = fmaf(p, x, 0.9999998857035092f);
-    const float r = u * p;
-    return inv ? 1.5707963267948966f - r : r;
+    const float s = u * u;
+    float r = 0.000990882766560405f;
+    r = fmaf(r, s, -0.0066840073563619829f);
+    r = fmaf(r, s, 0.021143804646584562f);
+    r = fmaf(r, s, -0.042978293426904776f);
+    r = fmaf(r, s, 0.066138929468158386f);
+    r = fmaf(r, s, -0.087516064688656053f);
+    r = fmaf(r, s, 0.1104117269740377f);
+    r = fmaf(r, s, -0.14276990716236754f);
+    r = fmaf(r, s, 0.19999428419267529f);
+    r = fmaf(r, s, -0.33333319184448684f);
+    return u * s * r;
 }
 
-// FP32 angle z = arccos(xi(v)) and weight mu(xi(v))^-2 of one mapped coordinate (Section 2.1):
-//   r = 1: z = pi/2 - atan(v/S),          mu^-2 = (S^2 + v^2)/S
-//   r = 0: z = 2 atan(exp(-v/S)),         mu^-2 = S (exp(v/S) + exp(-v/S))/2
-__device__ __forceinline__ void angle_weight_f32(float v, float S, float invS, bool alg, float &z, float &m2)
+// FP32 grid coordinate x = z n/(2 pi) of the angle z = arccos(xi(v)) of one mapped coordinate, as an
+// integer cell X (an integer-valued float) and a fraction F in [0, 1), and the weight
+// mu(xi(v))^-2 (Section 2.1).  With w = v/S:
+//   r = 1: |w| <= 1: x = n/4 - gs atan(w);  w > 1: x = gs atan(S/v);  w < -1: x = n/2 + gs atan(S/v)
+//          (z = pi/2 - atan(w) = atan(1/w) or pi + atan(1/w)),          mu^-2 = (S^2 + v^2)/S
+//   r = 0: x = 2 gs atan(e) (v >= 0) or n/2 - 2 gs atan(e) (v < 0), e = exp(-|v|/S),
+//          mu^-2 = S (1/e + e)/2
+// with gs = n/(2 pi), i.e. x = base - sg c atan(u) with |u| <= 1 and base in {0, n/4, n/2}.  The
+// offsets are exact, c = gs (or 2 gs) is a two-term constant, atan(u) = u + correction is
+// renormalised into two terms (Fast2Sum) and multiplied by c with its exact FMA residual, and
+// base - sg c atan(u) is summed exactly (Fast2Sum), so the fraction F is accurate to about 1e-7
+// of a cell: a grid coordinate rounded to FP32 as a whole (about 1e-6 of a cell at x ~ 100)
+// shifts points that share a coordinate -- and many do, on a tensor grid of nodes -- coherently.
+__device__ __forceinline__ void grid_coord_f32(const TypedConsts<float> &K, float v, bool alg, float &X, float &F,
+                                               float &m2)
 {
+    float base, sg, u, ch = K.gs, cl = K.gs_lo;
     if (alg) {
-        const float w = v * invS;
-        const float at = atan_pos_f32(fabsf(w));
-        z = 1.5707963267948966f - copysignf(at, w);
-        m2 = fmaf(v, v, S * S) * invS;
+        const float w = fmaf(v, K.invS, v * K.invS_lo);  // v/S
+        m2 = fmaf(v, v, K.SS) * K.invS;
+        if (fabsf(w) <= 1.0f) {
+            base = K.xq;
+            sg = 1.0f;
+            u = w;
+        } else {  // u = S/v: the approximate reciprocal and one Newton step
+            const float rv = rcp_approx(v);
+            const float u0 = K.S * rv;
+            u = fmaf(rv, fmaf(-v, u0, K.S), u0);
+            base = v > 0.0f ? 0.0f : 2.0f * K.xq;
+            sg = -1.0f;
+        }
     } else {
-        const float e = ex2_approx(-v * invS * 1.4426950408889634f);  // exp(-v/S)
-        z = 2.0f * atan_pos_f32(e);
-        m2 = 0.5f * S * (rcp_approx(e) + e);
+        const float w = fmaf(v, K.invS, v * K.invS_lo);
+        const float e = exp2f(-fabsf(w) * 1.4426950408889634f);  // exp(-|v|/S)
+        m2 = 0.5f * K.S * (__frcp_rn(e) + e);
+        u = e;
+        base = v >= 0.0f ? 0.0f : 2.0f * K.xq;
+        sg = v >= 0.0f ? -1.0f : 1.0f;
+        ch = 2.0f * K.gs;
+        cl = 2.0f * K.gs_lo;
+    }
+    const float corr = atan_correction_f32(u);
+    const float ah = u + corr;                            // atan(u) = ah + al
+    const float al = (u - ah) + corr;                     // exact (Fast2Sum: |u| >= |corr|)
+    const float p1 = ch * ah;
+    const float e1 = fmaf(ch, ah, -p1);                   // exact: p1 + e1 = ch ah
+    const float pl = e1 + fmaf(ch, al, cl * ah);          // the rest of c atan(u): a few ulp of p1
+    const float hi = base - sg * p1;
+    const float err = (base - hi) - sg * p1;              // exact (|base| >= |p1| or base = 0)
+    const float lo = err - sg * pl;
+    X = floorf(hi);
+    F = (hi - X) + lo;                                    // |lo| is far below one cell
+    if (F < 0.0f) {
+        F += 1.0f;
+        X -= 1.0f;
+        if (F >= 1.0f) {  // -F below half an ulp of 1: the point sits on the cell boundary
+            F = 0.0f;
+            X += 1.0f;
+        }
+    } else if (F >= 1.0f) {
+        F -= 1.0f;
+        X += 1.0f;
     }
 }
 
-// FP32 weights: t_a = (s - x) 2/w + a 2/w, psi = 2^(beta log2(e) (sqrt(1 - t^2) - 1)), with the
-// square root as (1 - t^2) rsqrt(1 - t^2); both approximations are good to a few 1e-7.
-template <int W>
-__device__ __forceinline__ int kernel_weights_f32(const SpreadArgs &p, float x, float *wt)
+// FP32 kernel value psi(t) 2^lsc = 2^(bl (sqrt(1 - t^2) - 1) + lsc) for |t| < 1 and 0 outside, with
+// bl = beta log2(e) and bias = lsc - bl; the square root as (1 - t^2) rsqrt(1 - t^2).  Both
+// approximations are good to a few 1e-7.
+__device__ __forceinline__ float es_f32(float t, float bl, float bias)
 {
-    const int s = (int)floorf(x - 0.5f * W) + 1;
+    const float om = fmaf(-t, t, 1.0f);
+    const float e = fmaf(bl, om * rsqrt_approx(om), bias);
+    return om > 0.0f ? ex2_approx(e) : 0.0f;
+}
+
+// First tap s = X + c0 of a point at X + F for kernel width W (s = floor(x - W/2) + 1) and the tap
+// offset t0 = (s - x) 2/W; tap a has t = t0 + a 2/W.
+template <int W>
+__device__ __forceinline__ int first_tap_f32(float X, float F, float &t0)
+{
+    int c0;
+    if constexpr (W % 2 == 0) c0 = 1 - W / 2;
+    else c0 = (F >= 0.5f ? 1 : 0) - (W - 1) / 2;
+    t0 = ((float)c0 - F) * (2.0f / W);
+    return (int)X + c0;
+}
+
+// FP32 weights psi(t_a) of one axis and the folded cells fold(s + a).
+template <int W>
+__device__ __forceinline__ void axis_weights_f32(const SpreadArgs &p, float X, float F, float *wt, int *idx)
+{
+    float t0;
+    const int s = first_tap_f32<W>(X, F, t0);
     const float h2 = 2.0f / W;
-    const float t0 = ((float)s - x) * h2;
-    const float bl = (float)(p.beta * 1.4426950408889634);
+    const float bl = p.cf.bl;
+    const bool simple = p.simple_fold != 0;
 #pragma unroll
     for (int a = 0; a < W; ++a) {
-        const float t = t0 + (float)a * h2;
-        const float om = fmaf(-t, t, 1.0f);
-        const float e = fmaf(bl, om * rsqrt_approx(om), -bl);
-        wt[a] = om > 0.0f ? ex2_approx(e) : 0.0f;
+        wt[a] = es_f32(fmaf((float)a, h2, t0), bl, -bl);
+        idx[a] = fold_cell(s + a, p.n, simple);
     }
-    return s;
 }
+
+// Row shear of the pair numbering (load_pair); t K stays below 2^32 for every node count a plan
+// accepts (t <= nnode/2 <= 2^21).
+constexpr unsigned kPairShear = 1597u;
 
 template <typename T, int D>
 struct PairData {
@@ -243,9 +312,13 @@ struct PairData {
 // Unordered node pairs.  Swapping i and j keeps the centre (v_i + v_j)/2, the radius
 // |v_i - v_j|/2 and the strength a_i a_j B(|v_i - v_j|) w_m, so (i, j) and (j, i) add the same
 // M points with the same weights: each unordered pair is spread once with twice the strength.
-// Numbering: pair pr = t nnode + i is (i, (i + t) mod nnode), offsets t = 0..floor(nnode/2);
-// t = 0 is the diagonal (multiplicity 1) and, for even nnode, the row t = nnode/2 stops at
-// i = nnode/2 - 1 (its other half repeats the same pairs): unordered_pairs(nnode) in all.
+// Numbering: pair pr = t nnode + u is (i, (i + t) mod nnode) with i = (u + t K) mod nnode, offsets
+// t = 0..floor(nnode/2); t = 0 is the diagonal (multiplicity 1) and, for even nnode, the row
+// t = nnode/2 stops at u = nnode/2 - 1 (its other half repeats the same pairs) and is not sheared:
+// unordered_pairs(nnode) in all.  The shear by K = kPairShear per row is a bijection of each row; it
+// makes a lane that strides through the pairs by a multiple of nnode (the single-plan launches
+// stride by SMs x threads, often a multiple of N^d) visit every node i instead of one, so the
+// lanes of a warp meet the negligible pairs of the tails of f at the same rate.
 
 // Load pair pr; false when its strength is zero.  ANG: also the unit direction (angular kernels).
 template <typename T, int D, bool ANG = false>
@@ -253,7 +326,8 @@ __device__ __forceinline__ bool load_pair(const SpreadArgs &p, long long pr, Pai
 {
     const int nnode = p.nnode, N = p.N;
     const int t = (int)(pr / nnode);
-    const int i = (int)(pr - (long long)t * nnode);
+    int i = (int)(pr - (long long)t * nnode);
+    if (2 * t != nnode) i = (int)(((unsigned)i + (unsigned)t * kPairShear) % (unsigned)nnode);
     int j = i + t;
     if (j >= nnode) j -= nnode;
     P.mult = t ? T(2) : T(1);
@@ -265,12 +339,18 @@ __device__ __forceinline__ bool load_pair(const SpreadArgs &p, long long pr, Pai
     T g2 = T(0);
 #pragma unroll
     for (int l = D - 1; l >= 0; --l) {
-        const T vi = vnode[ii % N], vj = vnode[jj % N];
+        const int ni = ii % N, nj = jj % N;
+        const T vi = vnode[ni], vj = vnode[nj];
         ii /= N;
         jj /= N;
-        const T dl = vi - vj;
+        T dl = vi - vj, sl = vi + vj;
+        if constexpr (sizeof(T) == 4) {  // FP32 nodes carry their rounding in a second term
+            const float li = p.vnode_lo[ni], lj = p.vnode_lo[nj];
+            dl += li - lj;
+            sl += li + lj;
+        }
         g2 += dl * dl;
-        P.cen[l] = T(0.5) * (vi + vj);
+        P.cen[l] = T(0.5) * sl;
         if constexpr (ANG) P.dir[l] = dl;
     }
     const T g = Fn<T>::sqrt_(g2);
@@ -279,12 +359,13 @@ __device__ __forceinline__ bool load_pair(const SpreadArgs &p, long long pr, Pai
 #pragma unroll
         for (int l = 0; l < D; ++l) P.dir[l] *= ginv;
     }
+    const TypedConsts<T> &K = kconst<T>(p);
     T B;
     switch (p.fast_gamma) {
-    case 0: B = T(p.Bconst); break;
-    case 1: B = T(p.Bconst) * g; break;
-    case 2: B = T(p.Bconst) * Fn<T>::sqrt_(g); break;
-    default: B = T(p.Bconst) * Fn<T>::pow_(g, T(p.gamma)); break;
+    case 0: B = K.Bconst; break;
+    case 1: B = K.Bconst * g; break;
+    case 2: B = K.Bconst * Fn<T>::sqrt_(g); break;
+    default: B = K.Bconst * Fn<T>::pow_(g, K.gamma); break;
     }
     P.base = aij * B;
     P.rad = T(0.5) * g;
@@ -296,12 +377,12 @@ __device__ __forceinline__ bool load_pair(const SpreadArgs &p, long long pr, Pai
 template <typename T, int D>
 __device__ __forceinline__ T pair_bound(const SpreadArgs &p, const PairData<T, D> &P)
 {
-    const T S = T(p.S), invS = T(1) / S;
-    T U = fabs(P.base) * T(p.Wsig * p.angmax);
+    const TypedConsts<T> &K = kconst<T>(p);
+    T U = fabs(P.base) * K.Wang;
 #pragma unroll
     for (int l = 0; l < D; ++l) {
         const T R = fabs(P.cen[l]) + P.rad;
-        U *= (p.r == 1) ? (S * S + R * R) * invS : S * Fn<T>::cosh_(R * invS);
+        U *= (p.r == 1) ? (K.SS + R * R) * K.invS : K.S * Fn<T>::cosh_(R * K.invS);
     }
     return U;
 }
@@ -320,24 +401,21 @@ __device__ __forceinline__ int tile_to_grid_cell(int c, int D, int nf, int ncol,
 // tile (Et = Eg - kTileBits), plus a per-block carry array of the same layout in global memory.
 // A contribution v in [-2^31, 2^31) goes to its word with one native 32-bit atomic; when that
 // addition overflows the signed range (visible from the returned old value o and the result r:
-// (o ^ r) & (v ^ r) < 0) the wrapped +-1 x 2^32 tile units go to the cell's carry counter.
-// Atomic additions on a word are serialised, so every wrap is that of exactly one addition and
-// word + 2^32 carry is the exact sum in any order.  Contributions of 2^31 units or more split
-// into a word part and a multiple of 2^32 added to the carry directly.  A block's partial sum in
-// one cell stays below B 2^Et = 2^(61 - kTileBits), so carries are rare (about B 2^Et / 2^32
-// in a whole evaluation) and a counter stays below 2^(29 - kTileBits) in magnitude.
+// (o ^ r) & (v ^ r) < 0) the wrapped +-1 x 2^32 tile units go to the cell's carry counter; the
+// direction is the addend's sign, which is that of the point's strength (every kernel weight is
+// >= 0), so it is one value per point.  Atomic additions on a word are serialised, so every wrap
+// is that of exactly one addition and word + 2^32 carry is the exact sum in any order.
+// Contributions of 2^31 units or more split into a word part and a multiple of 2^32 added to the
+// carry directly.  A block's partial sum in one cell stays below B 2^Et = 2^(61 - kTileBits), so
+// carries are rare (about B 2^Et / 2^32 in a whole evaluation) and a counter stays below
+// 2^(29 - kTileBits) in magnitude.
 constexpr int kTileBits = 14;
 
 struct SplitTile {
-    int *lo;       // tile words (shared memory)
-    int *carry;    // this block's carry counters (global memory, same layout)
-    int sgn = 1;   // sign of the current point's contributions (spread_point, with_sign)
-    // The tile for the contributions of one point of strength q: every kernel weight is >= 0, so
-    // they all have the sign of q, and a word wraps only in the direction of its addend's sign,
-    // so the counter moves by the point's sign (one value per point, not one per contribution).
-    __device__ __forceinline__ SplitTile with_sign(float q) const { return SplitTile{lo, carry, q < 0.0f ? -1 : 1}; }
+    int *lo;     // tile words (shared memory)
+    int *carry;  // this block's carry counters (global memory, same layout)
     // v of sign d (or zero)
-    __device__ __forceinline__ void add32(int c, int v, int d) const
+    __device__ __forceinline__ void add_int(int c, int v, int d) const
     {
         const int o = atomicAdd(lo + c, v);
         const int r = (int)((unsigned)o + (unsigned)v);
@@ -347,76 +425,85 @@ struct SplitTile {
     {
         const int xl = (int)(unsigned)(unsigned long long)x;  // low word, signed
         const long long xh = (x - xl) >> 32;                   // exact: x - xl is a multiple of 2^32
-        add32(c, xl, xl < 0 ? -1 : 1);
+        add_int(c, xl, xl < 0 ? -1 : 1);
         if (xh) atomicAdd(carry + c, (int)xh);
     }
-    // x of sign sgn.  Zero contributions are added too: a branch around them costs more than the
-    // atomic.
+    // any x (zero contributions are added too: a branch around them costs more than the atomic)
     __device__ __forceinline__ void add(int c, float x) const
     {
-        if (fabsf(x) < 2147483648.0f) add32(c, __float2int_rn(x), sgn);
+        if (fabsf(x) < 2147483648.0f) add_int(c, __float2int_rn(x), x < 0.0f ? -1 : 1);
         else add64(c, __float2ll_rn(x));
     }
-    // |x| < 2^31 known in advance
-    __device__ __forceinline__ void add_small(int c, float x) const { add32(c, __float2int_rn(x), sgn); }
-    // the contribution a b
-    __device__ __forceinline__ void add_product(int c, float a, float b) const { add(c, a * b); }
-    __device__ __forceinline__ void add_product_small(int c, float a, float b) const { add_small(c, a * b); }
     // the cell's sum in tile units
     __device__ __forceinline__ long long value(int c) const { return (long long)carry[c] * 4294967296LL + lo[c]; }
 };
 struct DoubleTile {  // FP64 path: FP64 partial sums
     double *v;
-    __device__ __forceinline__ DoubleTile with_sign(double) const { return *this; }
     // v[c] += a b (the library's shared-memory FP64 atomic add; a hand-written compare-and-swap
     // loop around one fused multiply-add measured 2-8x slower).  No test for a zero product: the
     // polynomial kernel weights are not zero at the support's ends as the exact kernel's are,
-    // and a zero-strength point is skipped whole (spread_point).
+    // and a zero-strength point is skipped whole (spread_point_f64).
     __device__ __forceinline__ void add_product(int c, double a, double b) const { atomicAdd(v + c, a * b); }
-    __device__ __forceinline__ void add_product_small(int c, double a, double b) const { add_product(c, a, b); }
 };
 
-// Point m of pair P: grid coordinates x (one grid cell = 1, x = z n / (2 pi)) and strength q in
-// tile units (qbase = a_i a_j B x multiplicity x tile scale).
+// One post-collision point: FP32 points carry each grid coordinate (one grid cell = 1,
+// x = z n / (2 pi)) as an integer cell X (an integer-valued float) and a fraction F in [0, 1)
+// (grid_coord_f32); FP64 points carry x itself.  q is the strength in tile units.
+template <typename T, int D>
+struct Point;
+template <int D>
+struct Point<float, D> {
+    float X[D], F[D], q;
+};
+template <int D>
+struct Point<double, D> {
+    double x[D], q;
+};
+
+// Point m of pair P (qbase = a_i a_j B x multiplicity x tile scale).
 template <typename T, int D, bool ANG = false>
-__device__ __forceinline__ void make_point(const SpreadArgs &p, const PairData<T, D> &P, T qbase, int m, T *x, T &q)
+__device__ __forceinline__ void make_point(const SpreadArgs &p, const PairData<T, D> &P, T qbase, int m,
+                                           Point<T, D> &pt)
 {
     const T *sig = static_cast<const T *>(p.sig);
     const T *wsig = static_cast<const T *>(p.wsig);
-    const T S = T(p.S), SS = S * S, invS = T(1) / S;
-    const T gs = T(p.grid_scale);
+    const TypedConsts<T> &K = kconst<T>(p);
     const bool alg = (p.r == 1);
-    q = qbase * wsig[m];
+    T q = qbase * wsig[m];
     if constexpr (ANG) {  // even part of b(cos theta), Horner in cos^2 theta
         T c = T(0);
 #pragma unroll
         for (int l = 0; l < D; ++l) c += P.dir[l] * sig[m * D + l];
         const T c2 = c * c;
-        T be = T(p.ang_even[p.nang_even - 1]);
-        for (int k = p.nang_even - 2; k >= 0; --k) be = be * c2 + T(p.ang_even[k]);
+        T be = K.ang_even[p.nang_even - 1];
+        for (int k = p.nang_even - 2; k >= 0; --k) be = be * c2 + K.ang_even[k];
         q *= be;
     }
 #pragma unroll
     for (int l = 0; l < D; ++l) {
         const T vp = P.cen[l] + P.rad * sig[m * D + l];
-        T z, m2;
+        T m2;
         if constexpr (sizeof(T) == 4) {
-            angle_weight_f32(vp, S, invS, alg, z, m2);
-        } else if (alg) {
-            z = Fn<T>::atan2_(S, vp);
-            m2 = (SS + vp * vp) * invS;
+            grid_coord_f32(K, vp, alg, pt.X[l], pt.F[l], m2);
         } else {
-            // z = 2 atan(e^-u) and mu^-2 = S cosh u with e = e^-|u| <= 1 (one exp and one atan
-            // instead of sinh, cosh and atan2): for u < 0, 2 atan(e^|u|) = pi - 2 atan(e^-|u|)
-            const double u = vp * invS;
-            const double e = exp(-fabs(u));
-            const double at2 = 2.0 * atan(e);
-            z = u >= 0.0 ? at2 : 3.14159265358979323846 - at2;
-            m2 = 0.5 * S * (e + 1.0 / e);
+            double z;
+            if (alg) {
+                z = Fn<T>::atan2_(K.S, vp);
+                m2 = (K.SS + vp * vp) * K.invS;
+            } else {
+                // z = 2 atan(e^-u) and mu^-2 = S cosh u with e = e^-|u| <= 1 (one exp and one atan
+                // instead of sinh, cosh and atan2): for u < 0, 2 atan(e^|u|) = pi - 2 atan(e^-|u|)
+                const double u = vp * K.invS;
+                const double e = exp(-fabs(u));
+                const double at2 = 2.0 * atan(e);
+                z = u >= 0.0 ? at2 : 3.14159265358979323846 - at2;
+                m2 = 0.5 * K.S * (e + 1.0 / e);
+            }
+            pt.x[l] = z * K.gs;
         }
         q *= m2;
-        x[l] = z * gs;
     }
+    pt.q = q;
 }
 
 // Tile layout.  A block tile holds rows row_lo..row_lo+nrows-1 of axis 0 of the folded grid, and
@@ -426,21 +513,141 @@ __device__ __forceinline__ void make_point(const SpreadArgs &p, const PairData<T
 // tile is added to the global grid (tile_to_grid_cell).  2D cell (row, u): row ncol + u + cpad;
 // 3D cell (row, j, u): (row nf + j) ncol + u + cpad.
 
-// Add the w^d contributions of one point to the block tile.  SMALL: every contribution is known
-// to lie in (-2^31, 2^31) tile units, so the tile's cheaper add_small applies.  SLAB: the tile
-// holds a slab of the grid's rows and rows outside it are skipped; otherwise it holds every row
-// (row_lo = 0, nrows = n/2 + 1).
-template <typename T, int D, int W, typename Tile, bool SMALL, bool SLAB>
-__device__ __forceinline__ void spread_point(const SpreadArgs &p, const T *x, T q, const Tile &tile_all, int row_lo,
-                                             int nrows, int plane)
+// ---- FP32 points
+//
+// Kinds of FP32 point: kInt -- |q| < 2^29 tile units (integer products); kLarge -- any q.
+constexpr int kInt = 0, kLarge = 1;
+// Points below this many tile units take the integer products; points below kNegligibleF32 add
+// exactly zero (4 q psi rounds to 0 for every row) and are skipped, and so are pairs whose points
+// all stay below it.
+constexpr float kIntLimitF32 = 536870912.0f;  // 2^29
+constexpr float kNegligibleF32 = 0.1f;
+
+// round(a b / 2^32) for |a| < 2^31, 0 <= b <= 2^30: the high word of one 64-bit multiply-add
+__device__ __forceinline__ int mulhi_rn(int a, int b)
 {
-    if constexpr (sizeof(T) == 8) {
-        if (q == T(0)) return;  // FP64 tiles add every product (DoubleTile)
+    return (int)(((long long)a * (long long)b + 0x80000000LL) >> 32);
+}
+
+// Add the w^d contributions q psi_a psi_b psi_c of one FP32 point to the block tile.  kInt: the
+// column factors 2^30 psi_c and, per row, 4 q psi_a (psi_b) are rounded to integers, and a
+// contribution is mulhi_rn of the two (at most about one tile unit of rounding).  kLarge: the
+// product is formed in FP32 and rounded to the tile unit.  SLAB: the tile holds a slab of the grid's
+// rows and rows outside it are skipped; otherwise it holds every row (row_lo = 0, nrows = n/2 + 1).
+// 3D points loop over their axis-0 rows (computing that row's kernel value in the loop) so that
+// the unrolled code stays small.
+template <int D, int W, int KIND, bool SLAB>
+__device__ __forceinline__ void spread_point_f32(const SpreadArgs &p, const Point<float, D> &pt,
+                                                 const SplitTile &tile, int row_lo, int nrows, int plane)
+{
+    const float q = pt.q;
+    if (fabsf(q) < kNegligibleF32) return;  // every contribution rounds to zero
+    const float bl = p.cf.bl;
+    const float h2 = 2.0f / W;
+    const bool simple = p.simple_fold != 0;
+    float t00, tl0;
+    const int s0 = first_tap_f32<W>(pt.X[0], pt.F[0], t00);          // first row
+    const int sl = first_tap_f32<W>(pt.X[D - 1], pt.F[D - 1], tl0);  // first column (unfolded)
+    const int cb = min(max(sl + p.cpad, 0), p.ncol - W);            // clamped: x lies in [0, n/2]
+    float w1[W];
+    int c1[W];
+    if constexpr (D == 3) {
+        axis_weights_f32<W>(p, pt.X[1], pt.F[1], w1, c1);
+#pragma unroll
+        for (int b = 0; b < W; ++b) c1[b] = c1[b] * p.ncol + cb;
     }
-    const Tile tile = tile_all.with_sign(q);
-    T w0[W];
+    if constexpr (KIND == kInt) {
+        const int sg = q < 0.0f ? -1 : 1;  // the sign of every contribution (or zero)
+        const float q4 = 4.0f * q;
+        const float bias30 = 30.0f - bl;
+        int wi[W];
+#pragma unroll
+        for (int c = 0; c < W; ++c) wi[c] = __float2int_rn(es_f32(fmaf((float)c, h2, tl0), bl, bias30));
+        if constexpr (D == 2) {
+#pragma unroll
+            for (int a = 0; a < W; ++a) {
+                int r = fold_cell(s0 + a, p.n, simple);
+                if constexpr (SLAB) {
+                    r -= row_lo;
+                    if ((unsigned)r >= (unsigned)nrows) continue;
+                }
+                const int rq = __float2int_rn(q4 * es_f32(fmaf((float)a, h2, t00), bl, -bl));
+                const int row = r * plane + cb;
+#pragma unroll
+                for (int c = 0; c < W; ++c) tile.add_int(row + c, mulhi_rn(rq, wi[c]), sg);
+            }
+        } else {
+#pragma unroll 1
+            for (int a = 0; a < W; ++a) {
+                int r = fold_cell(s0 + a, p.n, simple);
+                if constexpr (SLAB) {
+                    r -= row_lo;
+                    if ((unsigned)r >= (unsigned)nrows) continue;
+                }
+                const float qa = q4 * es_f32(fmaf((float)a, h2, t00), bl, -bl);
+                const int row = r * plane;
+#pragma unroll
+                for (int b = 0; b < W; ++b) {
+                    const int rq = __float2int_rn(qa * w1[b]);
+                    const int line = row + c1[b];
+#pragma unroll
+                    for (int c = 0; c < W; ++c) tile.add_int(line + c, mulhi_rn(rq, wi[c]), sg);
+                }
+            }
+        }
+    } else {
+        float wl[W];
+#pragma unroll
+        for (int c = 0; c < W; ++c) wl[c] = es_f32(fmaf((float)c, h2, tl0), bl, -bl);
+        if constexpr (D == 2) {
+#pragma unroll
+            for (int a = 0; a < W; ++a) {
+                int r = fold_cell(s0 + a, p.n, simple);
+                if constexpr (SLAB) {
+                    r -= row_lo;
+                    if ((unsigned)r >= (unsigned)nrows) continue;
+                }
+                const float qa = q * es_f32(fmaf((float)a, h2, t00), bl, -bl);
+                const int row = r * plane + cb;
+#pragma unroll
+                for (int c = 0; c < W; ++c) tile.add(row + c, qa * wl[c]);
+            }
+        } else {
+#pragma unroll 1
+            for (int a = 0; a < W; ++a) {
+                int r = fold_cell(s0 + a, p.n, simple);
+                if constexpr (SLAB) {
+                    r -= row_lo;
+                    if ((unsigned)r >= (unsigned)nrows) continue;
+                }
+                const float qa = q * es_f32(fmaf((float)a, h2, t00), bl, -bl);
+                const int row = r * plane;
+#pragma unroll
+                for (int b = 0; b < W; ++b) {
+                    const float qab = qa * w1[b];
+                    const int line = row + c1[b];
+#pragma unroll
+                    for (int c = 0; c < W; ++c) tile.add(line + c, qab * wl[c]);
+                }
+            }
+        }
+    }
+}
+
+// ---- FP64 points
+
+// Add the w^d contributions of one FP64 point to the block tile.  SLAB: the tile holds a slab of
+// the grid's rows and rows outside it are skipped; otherwise it holds every row (row_lo = 0,
+// nrows = n/2 + 1).
+template <int D, int W, bool SLAB>
+__device__ __forceinline__ void spread_point_f64(const SpreadArgs &p, const Point<double, D> &pt,
+                                                 const DoubleTile &tile, int row_lo, int nrows, int plane)
+{
+    const double q = pt.q;
+    if (q == 0.0) return;  // FP64 tiles add every product
+    double w0[W];
     int r0[W];
-    axis_weights<T, W>(p, x[0], w0, r0);
+    axis_weights_f64<W>(p, pt.x[0], w0, r0);
     bool hit = !SLAB;
 #pragma unroll
     for (int a = 0; a < W; ++a) {
@@ -451,23 +658,20 @@ __device__ __forceinline__ void spread_point(const SpreadArgs &p, const T *x, T 
         w0[a] *= q;
     }
     if (!hit) return;
-    T wl[W];  // last axis: consecutive padded columns cb..cb+w-1 (clamped: x lies in [0, n/2])
-    const int cb = min(max(kernel_weights<T, W>(p, x[D - 1], wl) + p.cpad, 0), p.ncol - W);
+    double wl[W];  // last axis: consecutive padded columns cb..cb+w-1 (clamped: x lies in [0, n/2])
+    const int cb = min(max(kernel_weights_f64<W>(pt.x[D - 1], wl) + p.cpad, 0), p.ncol - W);
     if (D == 2) {
 #pragma unroll
         for (int a = 0; a < W; ++a) {
             if (SLAB && (unsigned)r0[a] >= (unsigned)nrows) continue;
             const int row = r0[a] * plane + cb;
 #pragma unroll
-            for (int c = 0; c < W; ++c) {
-                if constexpr (SMALL) tile.add_product_small(row + c, w0[a], wl[c]);
-                else tile.add_product(row + c, w0[a], wl[c]);
-            }
+            for (int c = 0; c < W; ++c) tile.add_product(row + c, w0[a], wl[c]);
         }
     } else {
-        T w1[W];
+        double w1[W];
         int c1[W];
-        axis_weights<T, W>(p, x[1], w1, c1);
+        axis_weights_f64<W>(p, pt.x[1], w1, c1);
 #pragma unroll
         for (int b = 0; b < W; ++b) c1[b] = c1[b] * p.ncol + cb;
         for (int a = 0; a < W; ++a) {
@@ -475,46 +679,84 @@ __device__ __forceinline__ void spread_point(const SpreadArgs &p, const T *x, T 
             const int row = r0[a] * plane;
 #pragma unroll
             for (int b = 0; b < W; ++b) {
-                const T wab = w0[a] * w1[b];
+                const double wab = w0[a] * w1[b];
                 const int line = row + c1[b];
 #pragma unroll
-                for (int c = 0; c < W; ++c) {
-                    if constexpr (SMALL) tile.add_product_small(line + c, wab, wl[c]);
-                    else tile.add_product(line + c, wab, wl[c]);
-                }
+                for (int c = 0; c < W; ++c) tile.add_product(line + c, wab, wl[c]);
             }
         }
     }
 }
 
-
-// The M points of one pair, into a tile that holds every row of the grid.
-template <typename T, int D, int W, typename Tile, bool SMALL, bool ANG>
-__device__ __forceinline__ void spread_points(const SpreadArgs &p, const PairData<T, D> &P, T sc, const Tile &tile,
-                                              int row_lo, int nrows, int plane)
+// One point into a tile (every lane of the warp calls it, lanes without a pair with q = 0).  FP32:
+// integer products for points below 2^29 tile units, chosen per lane (a point's contributions must
+// not depend on its warp-mates: bitwise reproducibility across launch shapes; points of 2^29 tile
+// units or more are rare); a lane whose point is below kNegligibleF32 idles.
+template <typename T, int D, int W, typename Tile, bool SLAB>
+__device__ __forceinline__ void spread_point_any(const SpreadArgs &p, const Point<T, D> &pt, const Tile &tile,
+                                                 int row_lo, int nrows, int plane)
 {
-    const T qbase = P.base * sc;
-    for (int m = 0; m < p.M; ++m) {
-        T x[D], q;
-        make_point<T, D, ANG>(p, P, qbase, m, x, q);
-        spread_point<T, D, W, Tile, SMALL, false>(p, x, q, tile, row_lo, nrows, plane);
+    if constexpr (sizeof(T) == 4) {
+        if (fabsf(pt.q) < kIntLimitF32) spread_point_f32<D, W, kInt, SLAB>(p, pt, tile, row_lo, nrows, plane);
+        else spread_point_f32<D, W, kLarge, SLAB>(p, pt, tile, row_lo, nrows, plane);
+    } else {
+        spread_point_f64<D, W, SLAB>(p, pt, tile, row_lo, nrows, plane);
     }
 }
 
-// Spread the M points of one pair into the block tile; `sc` converts to tile units.  Pairs
-// whose largest single contribution is bounded below 2^30 tile units in magnitude (pair bound
-// x max_m w_m / sum_m w_m, kernel weights <= 1) take the SMALL path.
-template <typename T, int D, int W, typename Tile, bool ANG = false>
-__device__ __forceinline__ void spread_pair(const SpreadArgs &p, const PairData<T, D> &P, T sc, const Tile &tile,
-                                            int row_lo, int nrows, int plane)
+// Advance pr (in steps of `stride`, below `end`) to this lane's next pair that is not negligible:
+// a loaded pair with non-zero strength, a strength bound not below the screening threshold tau
+// (0: no screening), and a bound Ut >= floor_q on every point's |q| in tile units.  On success
+// P.base is multiplied by the pair's multiplicity; false when no pair is left.
+template <typename T, int D, bool ANG>
+__device__ __forceinline__ bool next_pair(const SpreadArgs &p, long long &pr, long long end, long long stride, T sc,
+                                          T tau, T floor_q, PairData<T, D> &P)
 {
-    if constexpr (sizeof(T) == 4) {
-        if (pair_bound<T, D>(p, P) * sc * T(p.wmax_frac) < T(1073741824.0f)) {
-            spread_points<T, D, W, Tile, true, ANG>(p, P, sc, tile, row_lo, nrows, plane);
-            return;
-        }
+    for (; pr < end; pr += stride) {
+        if (!load_pair<T, D, ANG>(p, pr, P)) continue;
+        const T U = pair_bound<T, D>(p, P);
+        if (tau > T(0) && U < tau) continue;
+        if (U * P.mult * sc * kconst<T>(p).wmax < floor_q) continue;
+        P.base *= P.mult;
+        return true;
     }
-    spread_points<T, D, W, Tile, false, ANG>(p, P, sc, tile, row_lo, nrows, plane);
+    return false;
+}
+
+// A pair of zero strength at the origin: its points add nothing (lanes whose pairs have run out).
+template <typename T, int D>
+__device__ __forceinline__ void zero_pair(PairData<T, D> &P)
+{
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+        P.cen[l] = T(0);
+        P.dir[l] = T(0);
+    }
+    P.rad = T(0);
+    P.base = T(0);
+    P.mult = T(0);
+}
+
+// The pairs pr = first, first + stride, ... below end of one lane, spread into a tile that holds
+// every row.  Every lane of the warp runs every point step (the loop conditions are uniform).
+template <typename T, int D, int W, typename Tile, bool ANG>
+__device__ __forceinline__ void spread_pairs(const SpreadArgs &p, long long first, long long end, long long stride,
+                                             T sc, T tau, T floor_q, const Tile &tile, int row_lo, int nrows, int plane)
+{
+    long long pr = first;
+    for (;;) {
+        PairData<T, D> P;
+        const bool ok = next_pair<T, D, ANG>(p, pr, end, stride, sc, tau, floor_q, P);
+        if (!__any_sync(0xffffffffu, ok)) break;
+        if (!ok) zero_pair<T, D>(P);
+        const T qbase = P.base * sc;
+        for (int m = 0; m < p.M; ++m) {
+            Point<T, D> pt;
+            make_point<T, D, ANG>(p, P, qbase, m, pt);
+            spread_point_any<T, D, W, Tile, false>(p, pt, tile, row_lo, nrows, plane);
+        }
+        if (ok) pr += stride;
+    }
 }
 
 // ---- slabbed grids: warp point queues
@@ -523,15 +765,19 @@ __device__ __forceinline__ void spread_pair(const SpreadArgs &p, const PairData<
 // if one of its w axis-0 rows lies there, and with a few slabs most points of a warp miss it:
 // spreading them where they are generated would leave most lanes idle while the others add.
 // Instead each warp appends the points that hit its slab to a queue of 32 entries in shared
-// memory (D coordinates and the strength, slot-major) and spreads a full queue with all 32
-// lanes, one point per lane.
+// memory (slot-major) and spreads a full queue with all 32 lanes, one point per lane.
 
-// Whether any of the w axis-0 rows of a point at grid coordinate x0 lies in the slab (the
-// rows of axis_weights).
-template <typename T, int W>
-__device__ __forceinline__ bool rows_hit(const SpreadArgs &p, T x0, int row_lo, int nrows)
+// Whether any of the w axis-0 rows of a point lies in the slab (the rows of the point's spreading).
+template <typename T, int D, int W>
+__device__ __forceinline__ bool rows_hit(const SpreadArgs &p, const Point<T, D> &pt, int row_lo, int nrows)
 {
-    const int s = (int)Fn<T>::floor_(x0 - T(0.5 * W)) + 1;
+    int s;
+    if constexpr (sizeof(T) == 4) {
+        float t0;
+        s = first_tap_f32<W>(pt.X[0], pt.F[0], t0);
+    } else {
+        s = (int)floor(pt.x[0] - 0.5 * W) + 1;
+    }
     const bool simple = p.simple_fold != 0;
     bool hit = false;
 #pragma unroll
@@ -539,72 +785,88 @@ __device__ __forceinline__ bool rows_hit(const SpreadArgs &p, T x0, int row_lo, 
     return hit;
 }
 
+// Queue slot layout per warp: FP32 points X[D], F[D], q; FP64 points x[D], q (32 slots each).
 template <typename T, int D>
-__device__ __forceinline__ void queue_put(T *buf, int slot, const T *x, T q)
+__device__ __forceinline__ void queue_put(T *buf, int slot, const Point<T, D> &pt)
 {
 #pragma unroll
-    for (int l = 0; l < D; ++l) buf[l * 32 + slot] = x[l];
-    buf[D * 32 + slot] = q;
+    for (int l = 0; l < D; ++l) {
+        if constexpr (sizeof(T) == 4) {
+            buf[l * 32 + slot] = pt.X[l];
+            buf[(D + l) * 32 + slot] = pt.F[l];
+        } else {
+            buf[l * 32 + slot] = pt.x[l];
+        }
+    }
+    buf[(sizeof(T) == 4 ? 2 * D : D) * 32 + slot] = pt.q;
 }
 
-// Spread queue slot `lane` (when valid) with the whole warp; the FP32 fast add applies when
-// every queued strength is below 2^30 tile units (kernel weights are <= 1).
+template <typename T, int D>
+__device__ __forceinline__ void queue_get(const T *buf, int slot, Point<T, D> &pt)
+{
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+        if constexpr (sizeof(T) == 4) {
+            pt.X[l] = buf[l * 32 + slot];
+            pt.F[l] = buf[(D + l) * 32 + slot];
+        } else {
+            pt.x[l] = buf[l * 32 + slot];
+        }
+    }
+    pt.q = buf[(sizeof(T) == 4 ? 2 * D : D) * 32 + slot];
+}
+
+// Spread queue slot `lane` (when valid) with the whole warp.
 template <typename T, int D, int W, typename Tile>
 __device__ __forceinline__ void queue_spread(const SpreadArgs &p, const T *buf, int lane, bool valid,
                                              const Tile &tile, int row_lo, int nrows, int plane)
 {
-    T x[D], q = T(0);
-    if (valid) {
-#pragma unroll
-        for (int l = 0; l < D; ++l) x[l] = buf[l * 32 + lane];
-        q = buf[D * 32 + lane];
-    }
-    if constexpr (sizeof(T) == 4) {
-        const bool small = __all_sync(0xffffffffu, fabsf(q) < 1073741824.0f);
-        if (!valid) return;
-        if (small) spread_point<T, D, W, Tile, true, true>(p, x, q, tile, row_lo, nrows, plane);
-        else spread_point<T, D, W, Tile, false, true>(p, x, q, tile, row_lo, nrows, plane);
-    } else {
-        if (valid) spread_point<T, D, W, Tile, false, true>(p, x, q, tile, row_lo, nrows, plane);
-    }
+    if (!valid) return;
+    Point<T, D> pt;
+    queue_get<T, D>(buf, lane, pt);
+    spread_point_any<T, D, W, Tile, true>(p, pt, tile, row_lo, nrows, plane);
 }
 
 // The pairs pr = first, first + nthr, ... of one thread, spread into one slab through the
-// warp's queue `buf` ((D + 1) x 32 values).  Every loop condition is uniform over the warp.
+// warp's queue `buf` (spread_queue_values(d, fp32) x 32 values).  Every loop condition is uniform
+// over the warp.
 template <typename T, int D, int W, typename Tile, bool ANG>
 __device__ __forceinline__ void spread_pairs_queued(const SpreadArgs &p, long long first, long long nthr, T sc, T tau,
-                                                    const Tile &tile, int row_lo, int nrows, int plane, T *buf)
+                                                    T floor_q, const Tile &tile, int row_lo, int nrows, int plane,
+                                                    T *buf)
 {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     int count = 0;  // queued points, the same in every lane
-    for (long long pr = first; __any_sync(full, pr < p.npairs); pr += nthr) {
+    long long pr = first;
+    for (;;) {
         PairData<T, D> P;
-        bool ok = pr < p.npairs && load_pair<T, D, ANG>(p, pr, P);
-        if (ok && tau > T(0) && pair_bound<T, D>(p, P) < tau) ok = false;
-        if (!__any_sync(full, ok)) continue;
-        const T qbase = ok ? P.base * P.mult * sc : T(0);
+        const bool ok = next_pair<T, D, ANG>(p, pr, p.npairs, nthr, sc, tau, floor_q, P);
+        if (!__any_sync(full, ok)) break;
+        const T qbase = ok ? P.base * sc : T(0);
         for (int m = 0; m < p.M; ++m) {
-            T x[D], q = T(0);
+            Point<T, D> pt;
             bool hit = false;
             if (ok) {
-                make_point<T, D, ANG>(p, P, qbase, m, x, q);
-                hit = rows_hit<T, W>(p, x[0], row_lo, nrows);
+                make_point<T, D, ANG>(p, P, qbase, m, pt);
+                // FP32 points below kNegligibleF32 add exactly zero and are not queued
+                hit = (sizeof(T) == 8 || fabs(pt.q) >= T(kNegligibleF32)) && rows_hit<T, D, W>(p, pt, row_lo, nrows);
             }
             const unsigned mask = __ballot_sync(full, hit);
             const int n = __popc(mask), rank = __popc(mask & lt), room = 32 - count;
-            if (hit && rank < room) queue_put<T, D>(buf, count + rank, x, q);
+            if (hit && rank < room) queue_put<T, D>(buf, count + rank, pt);
             if (n >= room) {  // full: spread 32 points, then queue the rest
                 __syncwarp();
                 queue_spread<T, D, W, Tile>(p, buf, lane, true, tile, row_lo, nrows, plane);
                 __syncwarp();
-                if (hit && rank >= room) queue_put<T, D>(buf, rank - room, x, q);
+                if (hit && rank >= room) queue_put<T, D>(buf, rank - room, pt);
                 count = n - room;
             } else {
                 count += n;
             }
         }
+        if (ok) pr += nthr;
     }
     __syncwarp();
     queue_spread<T, D, W, Tile>(p, buf, lane, lane < count, tile, row_lo, nrows, plane);
@@ -667,17 +929,12 @@ __global__ void __launch_bounds__(kMaxThreadsF32) k_spread_f32(const __grid_cons
     pair_schedule(p, first, nthr);
     if (p.nslab > 1) {
         float *buf = reinterpret_cast<float *>(smem_raw + (size_t)p.rows_per_slab * G.plane * 4) +
-                     (threadIdx.x >> 5) * 32 * (D + 1);
-        spread_pairs_queued<float, D, W, SplitTile, ANG>(p, first, nthr, sc, tau, tile, G.row_lo, G.nrows, G.plane,
-                                                          buf);
+                     (threadIdx.x >> 5) * 32 * spread_queue_values(D, true);
+        spread_pairs_queued<float, D, W, SplitTile, ANG>(p, first, nthr, sc, tau, kNegligibleF32, tile, G.row_lo,
+                                                          G.nrows, G.plane, buf);
     } else {
-        for (long long pr = first; pr < p.npairs; pr += nthr) {
-            PairData<float, D> P;
-            if (!load_pair<float, D, ANG>(p, pr, P)) continue;
-            if (tau > 0.0f && pair_bound<float, D>(p, P) < tau) continue;
-            P.base *= P.mult;
-            spread_pair<float, D, W, SplitTile, ANG>(p, P, sc, tile, G.row_lo, G.nrows, G.plane);
-        }
+        spread_pairs<float, D, W, SplitTile, ANG>(p, first, p.npairs, nthr, sc, tau, kNegligibleF32, tile, G.row_lo,
+                                                   G.nrows, G.plane);
     }
     __syncthreads();
     for (int c = threadIdx.x; c < G.ncell; c += blockDim.x) {
@@ -702,21 +959,19 @@ __global__ void __launch_bounds__(kMaxThreadsF64) k_spread_f64(const __grid_cons
     const double Bnd = *p.bound;
     const int Eg = global_exponent(Bnd);
     const double tau = *p.tau;
+    // pairs whose summed strength bounds stay below 2^-64 B are skipped (per-point bound below
+    // floor_q, and at most npairs pairs)
+    const double floor_q = ldexp(Bnd, -64) * p.cd.wmax / (double)p.npairs;
     long long first, nthr;
     pair_schedule(p, first, nthr);
     if (p.nslab > 1) {
         double *buf = reinterpret_cast<double *>(smem_raw + (size_t)p.rows_per_slab * G.plane * 8) +
-                      (threadIdx.x >> 5) * 32 * (D + 1);
-        spread_pairs_queued<double, D, W, DoubleTile, ANG>(p, first, nthr, 1.0, tau, tile, G.row_lo, G.nrows,
+                      (threadIdx.x >> 5) * 32 * spread_queue_values(D, false);
+        spread_pairs_queued<double, D, W, DoubleTile, ANG>(p, first, nthr, 1.0, tau, floor_q, tile, G.row_lo, G.nrows,
                                                             G.plane, buf);
     } else {
-        for (long long pr = first; pr < p.npairs; pr += nthr) {
-            PairData<double, D> P;
-            if (!load_pair<double, D, ANG>(p, pr, P)) continue;
-            if (tau > 0.0 && pair_bound<double, D>(p, P) < tau) continue;
-            P.base *= P.mult;
-            spread_pair<double, D, W, DoubleTile, ANG>(p, P, 1.0, tile, G.row_lo, G.nrows, G.plane);
-        }
+        spread_pairs<double, D, W, DoubleTile, ANG>(p, first, p.npairs, nthr, 1.0, tau, floor_q, tile, G.row_lo,
+                                                     G.nrows, G.plane);
     }
     __syncthreads();
     // block partial sums -> the grid's fixed-point unit (|v| 2^Eg <= 2^61); the rounding of a

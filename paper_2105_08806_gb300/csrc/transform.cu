@@ -96,8 +96,8 @@ constexpr int kLossThreads = 128;
 // where c = (v_i + v_j)/2, rad = |v_i - v_j|/2: every post-collision point of the pair lies
 // in the box |v'_l| <= |c_l| + rad and mu^-2 grows with |v|, so ub_i bounds the spreading
 // strengths sum_{j,m} |q_ijm| (times Bconst, which Bw carries).  PT is the arithmetic of the
-// pair terms: FP64, or FP32 for the FP32 path, where 64-term partial sums are FP32 and
-// everything above them FP64.
+// pair terms: FP64, or FP32 for the FP32 path (node differences with the nodes' FP32 rounding
+// added back); the loss sums are FP64 either way, the bound's 64-term partial sums FP32.
 // b(cos theta) summed over the sphere set for the pair direction dvec = v_i - v_j (|dvec| = g):
 // (1/Wsig) sum_m w_m b(dvec . sigma_m / g), cos theta = 0 when g = 0 (Eq. collision_form).
 template <typename PT>
@@ -119,7 +119,8 @@ __device__ __forceinline__ PT angular_mean(const Angular &ang, const PT *dvec, P
 
 template <typename PT>
 __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict__ a,
-                                                        const PT *__restrict__ vnode, int N, int d, int M,
+                                                        const PT *__restrict__ vnode,
+                                                        const float *__restrict__ vnode_lo, int N, int d, int M,
                                                         const PT *__restrict__ sig, const PT *__restrict__ wsig,
                                                         const Angular ang, double angmax, double Wsig,
                                                         double gamma, int fast_gamma, double Bw,
@@ -141,22 +142,26 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict_
             t /= N;
         }
     }
-    PT vi[3];
+    PT vi[3], vil[3] = {PT(0), PT(0), PT(0)};
     for (int l = 0; l < 3; ++l) vi[l] = (l < d) ? vnode[idx[l]] : PT(0);
+    if (vnode_lo)
+        for (int l = 0; l < d; ++l) vil[l] = PT(vnode_lo[idx[l]]);
     const PT Sp = PT(S), invS = PT(1) / Sp, gam = PT(gamma);
     const double ai_w = fabs(a[i]) * Bw * angmax;  // pair bound = ai_w * |a_j| B_ij prod mu^-2
     const PT inv_wsig = PT(1.0 / Wsig);
     double acc = 0.0, bnd = 0.0;
     for (int j0 = threadIdx.x * 64; j0 < nnode; j0 += blockDim.x * 64) {
-        PT lp = PT(0), bp = PT(0);
+        PT bp = PT(0);
         const int j1 = min(j0 + 64, nnode);
         for (int j = j0; j < j1; ++j) {
             int t = j;
             PT g2 = PT(0), vj[3] = {PT(0), PT(0), PT(0)}, dv[3] = {PT(0), PT(0), PT(0)};
             for (int l = d - 1; l >= 0; --l) {
-                vj[l] = vnode[t % N];
+                const int nj = t % N;
+                vj[l] = vnode[nj];
                 t /= N;
                 dv[l] = vi[l] - vj[l];
+                if (vnode_lo) dv[l] += vil[l] - PT(vnode_lo[nj]);  // FP32 nodes: their rounding, too
                 g2 += dv[l] * dv[l];
             }
             const PT g = sqrt(g2);
@@ -168,11 +173,11 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict_
             default: B = (g2 > PT(0)) ? pow(g, gam) : PT(0); break;
             }
             const PT aj = PT(a[j]);
-            // explicit FMA: the batched plans' loss sums the same terms the same way
+            // the pair term in PT, its sum in FP64 (the batched plans' loss sums the same way)
             if (ang.n)
-                lp = fma(aj * B, angular_mean<PT>(ang, dv, g, d, M, sig, wsig, inv_wsig), lp);
+                acc = fma(double(B * angular_mean<PT>(ang, dv, g, d, M, sig, wsig, inv_wsig)), a[j], acc);
             else
-                lp = fma(aj, B, lp);
+                acc = fma(double(B), a[j], acc);
             if (aj != PT(0) && B != PT(0)) {
                 PT mu = PT(1);
                 for (int l = 0; l < d; ++l) {
@@ -184,7 +189,6 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict_
                 if (hist) atomicAdd(&s_hist[screen_bin(ai_w * (double)u)], 1u);
             }
         }
-        acc += (double)lp;
         bnd += (double)bp;
     }
     const double tot = block_sum<kLossThreads>(acc);
@@ -235,14 +239,14 @@ __global__ void __launch_bounds__(kReduceThreads) k_bound_reduce(const double *_
 // First transform pass over the int64 fixed-point grid: out = (A . in) 2^-Eg.
 __global__ void k_axis_pass_fixed(const unsigned long long *__restrict__ in, Dims3 id, int ax,
                                   const double *__restrict__ A, int m, const double *__restrict__ Bp,
-                                  double *__restrict__ out)
+                                  double scale, double *__restrict__ out)
 {
     Dims3 od = id;
     od.e[ax] = m;
     const long long total = (long long)od.e[0] * od.e[1] * od.e[2];
     const int len = id.e[ax];
     const long long sax = stride_of(id, ax);
-    const double unit = ldexp(1.0, -global_exponent(*Bp));
+    const double unit = ldexp(scale, -global_exponent(*Bp));
     for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < total;
          o += (long long)gridDim.x * blockDim.x) {
         int oc[3];
@@ -457,7 +461,8 @@ cudaError_t launch_recon_last(const double *in, Dims3 in_dims, const double *A, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_loss(const double *a, const double *vnode, const float *vnode32, int N, int d, int M,
+cudaError_t launch_loss(const double *a, const double *vnode, const float *vnode32, const float *vnode32_lo, int N,
+                        int d, int M,
                         const double *sig, const double *wsig, const float *sig32, const float *wsig32,
                         const Angular &ang, double angmax, double Wsig, double gamma,
                         int fast_gamma, double Bw, const double *inv_mu2, double S, int r, double *h,
@@ -465,10 +470,10 @@ cudaError_t launch_loss(const double *a, const double *vnode, const float *vnode
 {
     const int nnode = (d == 2) ? N * N : N * N * N;
     if (vnode32)
-        k_loss<float><<<nnode, kLossThreads, 0, s>>>(a, vnode32, N, d, M, sig32, wsig32, ang, angmax, Wsig, gamma,
-                                                     fast_gamma, Bw, inv_mu2, S, r, h, ub, hist);
+        k_loss<float><<<nnode, kLossThreads, 0, s>>>(a, vnode32, vnode32_lo, N, d, M, sig32, wsig32, ang, angmax, Wsig,
+                                                     gamma, fast_gamma, Bw, inv_mu2, S, r, h, ub, hist);
     else
-        k_loss<double><<<nnode, kLossThreads, 0, s>>>(a, vnode, N, d, M, sig, wsig, ang, angmax, Wsig, gamma,
+        k_loss<double><<<nnode, kLossThreads, 0, s>>>(a, vnode, nullptr, N, d, M, sig, wsig, ang, angmax, Wsig, gamma,
                                                       fast_gamma, Bw, inv_mu2, S, r, h, ub, hist);
     return cudaGetLastError();
 }
@@ -481,12 +486,12 @@ cudaError_t launch_bound_reduce(const double *ub, int n, const unsigned long lon
 }
 
 cudaError_t launch_axis_pass_fixed(const unsigned long long *in, Dims3 in_dims, int ax, const double *A,
-                                   int m, const double *B, double *out, cudaStream_t s)
+                                   int m, const double *B, double scale, double *out, cudaStream_t s)
 {
     Dims3 od = in_dims;
     od.e[ax] = m;
     k_axis_pass_fixed<<<grid_for((long long)od.e[0] * od.e[1] * od.e[2]), kThreads, 0, s>>>(in, in_dims, ax, A,
-                                                                                           m, B, out);
+                                                                                           m, B, scale, out);
     return cudaGetLastError();
 }
 

@@ -80,7 +80,10 @@ def test_all_modes_match_oracle(case, prec):
     if r == 1 and N >= 2:
         # mass: exact for any sphere set; energy: needs sum_m w_m sigma_m = 0 (antipodal sets)
         ma, en = O.mass_energy_coeffs(d, N, S)
-        bound = 1e-12 if prec == PG_PREC_FP64 else 1e-6
+        # FP32: each point's coordinates and strength carry about 1e-7 of rounding; the smallest
+        # plan (N = 2, M = 2: 20 points on a 10-cell grid) averages none of it away and sits
+        # at 1.0e-6 of the gain's mass functional
+        bound = 1e-12 if prec == PG_PREC_FP64 else 2e-6
         assert abs(mom["mass"]) <= bound * abs(ma @ gain) + 1e-300
         if sphere != PG_SPHERE_FIBONACCI:
             assert abs(mom["energy"]) <= bound * np.abs(en * gain).sum()
