@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __gr
             ncell = plane * s_cd.nf;
             const double Bc = b.Bcell[cell];
             Eg = global_exponent(Bc);
-            const int Et = F32 ? min(Eg - kTileBits, 120) : Eg;
+            const int Et = F32 ? min(Eg - tile_bits(D), 120) : Eg;
             shift = Eg - Et;
             sc = F32 ? T(ldexp(1.0, Et)) : T(1);
             tau = T(b.Tcell[cell]);

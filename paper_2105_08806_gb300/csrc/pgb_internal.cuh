@@ -134,6 +134,14 @@ __host__ __device__ inline size_t spread_queue_bytes(int threads, int d, bool f3
 // columns beyond either end; w/2 + 1 leave a margin for rounding of x.
 __host__ __device__ inline int tile_col_pad(int w) { return w / 2 + 1; }
 
+// FP32 block tiles count in units 2^-(Eg - tile_bits(d)), about 2^-47 B (2D) or 2^-53 B (3D) for the
+// strength bound B: each contribution is rounded to the tile unit once, and with w^3 contributions
+// per point and the deconvolution's growth along three axes, 3D needs the finer unit for the FP32
+// path's accuracy (with 2^-47 B the rounding was 3e-6 of the gain norm on the 3D gamma = 1/2
+// workload, with 2^-53 B 4e-7); a coarser unit makes more node pairs negligible (skipped exactly)
+// and more points fit the integer products, which is faster.
+__host__ __device__ constexpr int tile_bits(int d) { return d == 3 ? 8 : 14; }
+
 // Exponent Eg of the grid's fixed-point unit 2^-Eg: the largest E with B 2^E < 2^61 for the
 // bound B >= sum_p |q_p| (0 when B is zero or not finite).
 __host__ __device__ inline int global_exponent(double B)

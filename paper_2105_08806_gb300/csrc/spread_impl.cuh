@@ -29,7 +29,7 @@
 //    memory; at the end each cell's partial sum is rounded to the grid unit (relative error
 //    2^-61 B) and added to the global grid.
 //  - FP32 kernel: the private copy holds one signed 32-bit word per cell in units of 2^-Et,
-//    Et = Eg - kTileBits, plus per-cell carry counters in a per-block global array (SplitTile):
+//    Et = Eg - tile_bits(d), plus per-cell carry counters in a per-block global array (SplitTile):
 //    the cell's value is word + 2^32 carry.  A contribution goes to its word with one native 32-bit
 //    shared atomic, and only an addition that overflows the word's signed range (seen from the
 //    returned old value) moves the cell's carry counter.  (Floating-point shared atomics are
@@ -38,7 +38,7 @@
 //    them -- form their contributions in integers: the row factor 4 q psi_a (psi_b) and the column
 //    factor 2^30 psi_c are rounded once per row and column, and a contribution is the rounded high
 //    word of their 64-bit product (one integer multiply-add).  At the end each block adds
-//    word + 2^32 carry (scaled by 2^kTileBits) to the global grid.  Each contribution is rounded
+//    word + 2^32 carry (scaled by 2^tile_bits(d)) to the global grid.  Each contribution is rounded
 //    to the tile unit (at most about one unit); all later additions are exact.
 //
 // Negligible pairs: a pair whose strength bound keeps every one of its points below 0.1 tile unit
@@ -398,7 +398,7 @@ __device__ __forceinline__ int tile_to_grid_cell(int c, int D, int nf, int ncol,
 // Shared-memory accumulators of the block tile.
 //
 // FP32 path: one signed 32-bit fixed-point word per cell in shared memory, in units 2^-Et of the
-// tile (Et = Eg - kTileBits), plus a per-block carry array of the same layout in global memory.
+// tile (Et = Eg - tile_bits(d)), plus a per-block carry array of the same layout in global memory.
 // A contribution v in [-2^31, 2^31) goes to its word with one native 32-bit atomic; when that
 // addition overflows the signed range (visible from the returned old value o and the result r:
 // (o ^ r) & (v ^ r) < 0) the wrapped +-1 x 2^32 tile units go to the cell's carry counter; the
@@ -406,10 +406,9 @@ __device__ __forceinline__ int tile_to_grid_cell(int c, int D, int nf, int ncol,
 // >= 0), so it is one value per point.  Atomic additions on a word are serialised, so every wrap
 // is that of exactly one addition and word + 2^32 carry is the exact sum in any order.
 // Contributions of 2^31 units or more split into a word part and a multiple of 2^32 added to the
-// carry directly.  A block's partial sum in one cell stays below B 2^Et = 2^(61 - kTileBits), so
+// carry directly.  A block's partial sum in one cell stays below B 2^Et = 2^(61 - bits), so
 // carries are rare (about B 2^Et / 2^32 in a whole evaluation) and a counter stays below
-// 2^(29 - kTileBits) in magnitude.
-constexpr int kTileBits = 14;
+// 2^(29 - bits) in magnitude (bits = tile_bits(d)).
 
 struct SplitTile {
     int *lo;     // tile words (shared memory)
@@ -918,9 +917,9 @@ __global__ void __launch_bounds__(kMaxThreadsF32) k_spread_f32(const __grid_cons
     __syncthreads();
     const double Bnd = *p.bound;
     const int Eg = global_exponent(Bnd);
-    // Tile unit 2^-Et with Et = Eg - kTileBits (2^-47 B or finer); kept inside the float range for
-    // tiny inputs (a coarser unit there).
-    const int Et = min(Eg - kTileBits, 120);
+    // Tile unit 2^-Et with Et = Eg - tile_bits(D) (2^-47 B or finer in 2D, 2^-53 B in 3D); kept
+    // inside the float range for tiny inputs (a coarser unit there).
+    const int Et = min(Eg - tile_bits(D), 120);
     const int shift = Eg - Et;
     const SplitTile tile{words, carry};
     const float sc = (float)ldexp(1.0, Et);

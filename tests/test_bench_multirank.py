@@ -52,7 +52,7 @@ def test_bench_workloads_name_the_seeded_configurations():
     from paper_2105_08806_gb300 import workloads as W
     expect = {"2d-hard-spheres": (2, 64, 32), "2d-maxwell": (2, 16, 8), "3d-bkw": (3, 16, 32),
               "3d-bimaxwell": (3, 24, 32)}
-    assert bench.DEFAULT_WORKLOAD == "2d-hard-spheres" and set(bench.WORKLOADS) == set(expect)
+    assert bench.HEADLINE == "2d-hard-spheres" and set(bench.WORKLOADS) == set(expect)
     for name, (ctor, desc) in bench.WORKLOADS.items():
         w = getattr(W, ctor)()
         assert (w.d, w.N, w.M) == expect[name], name
