@@ -75,6 +75,8 @@ def parse():
                     help="run the batched workload on its first K cells only (0: all 4096; for profiling)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=None,
                     help="measure this single-plan workload only (for profiling)")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="measure the batched workload only, beside the headline's FP32 path (for profiling)")
     ap.add_argument("--sphere-points", type=int, default=0,
                     help="override the workload's number of sphere points M (0: the workload's own; for "
                          "profiling the same kernel on a smaller case)")
@@ -576,14 +578,14 @@ def run_ours(args):
              "basis": "measured on this GPU: pg_boltz_probe_pipes (FMA chains, conflict-free shared atomics) and "
                       "pg_boltz_probe_shared_atomics (random addresses of a 16,900-cell tile)"}
     head = args.workload or HEADLINE
-    names = [head] + ([] if args.workload else [n for n in WORKLOADS if n != head])
+    names = [head] + ([] if (args.workload or args.batched_only) else [n for n in WORKLOADS if n != head])
     with ClockSampler(local, enabled=not args.no_clocks) as clk:
         rows = {head: measure_config(head, args, dev, stream, timer, peaks, world)}
     clocks = clk.summary()
     for n in names[1:]:
         rows[n] = measure_config(n, args, dev, stream, timer, peaks, world)
-    e2e, screened = (headline_extras(args, dev, stream, timer, world) if head == HEADLINE and args.sphere_points == 0
-                     else (None, None))
+    e2e, screened = (headline_extras(args, dev, stream, timer, world)
+                     if head == HEADLINE and args.sphere_points == 0 and not args.batched_only else (None, None))
     batched = None
     if not args.no_batched and not args.workload:
         batched = run_batched(max(1, args.batched_steps), stream, dev, args.batched_cells)

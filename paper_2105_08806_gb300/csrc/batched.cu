@@ -311,6 +311,7 @@ __device__ __forceinline__ void cell_args(const BatchArgs &b, const CellDesc &cd
     sa.cpad = tile_col_pad(b.w);
     sa.ncol = cd.nf + 2 * sa.cpad;
     sa.kpoly = b.kpoly;
+    sa.queued = 0;
     fill_spread_consts(sa);
 }
 

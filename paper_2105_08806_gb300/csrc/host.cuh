@@ -119,6 +119,7 @@ struct pg_boltz_plan_s {
     float *v32 = nullptr;
     float *v32lo = nullptr;  // v - (double)v32: the FP32 nodes' rounding
     double grid_scale_corr = 1.0;  // FP32 plans: exact / FP32 constant factors of the strengths
+    int queued = 0;                // FP32 one-slab plans: point queues beside the tile (SpreadArgs::queued)
     double *sig64 = nullptr, *wsig64 = nullptr;  // M x d, M
     float *sig32 = nullptr, *wsig32 = nullptr;
     // workspace

@@ -70,6 +70,8 @@ struct SpreadArgs {
     int ncol;             // nf + 2 cpad: tile cells along the last axis
     int tile_cells;       // cells of one block tile (rows_per_slab rows)
     int *carry;           // FP32: per-block carry counters, blocks x tile_cells (global memory)
+    int queued;           // FP32 one-slab grids: 1 when the warps' point queues follow the tile in
+                          // shared memory (spread_queue_bytes of the launch's threads)
     // angular kernel: a spread pair stands for both orders, whose cos theta differ in sign, so
     // the gain needs the even part b_e(c) = (b(c) + b(-c))/2 = sum_k ang_even[k] c^(2k) only
     int nang_even;        // terms of ang_even; 0: VHS kernel (no angular factor)

@@ -153,6 +153,16 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
         return set_error(PG_ERR_ARG, "spread_threads must be a multiple of 32 and <= %d", max_threads);
     if (p->nslab > 1 && pgb::spread_queue_bytes(p->spread_threads, d, f32) > qbytes)
         return set_error(PG_ERR_STATE, "internal: point queues larger than reserved");
+    // FP32 one-slab grids: the warps also queue their points that add something and spread full
+    // queues (every lane busy), when the queues fit beside the tile
+    p->queued = 0;
+    if (f32 && p->nslab == 1) {
+        const size_t qq = pgb::spread_queue_bytes(p->spread_threads, d, true);
+        if (p->spread_smem + qq <= max_smem) {
+            p->queued = 1;
+            p->spread_smem += qq;
+        }
+    }
     per_sm = std::min(per_sm, prop.maxThreadsPerMultiProcessor / p->spread_threads);
     if (o.spread_blocks_per_sm > 0) per_sm = std::min(per_sm, o.spread_blocks_per_sm);
     per_sm = std::max(per_sm, 1);
@@ -211,6 +221,7 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
     ka.ncol = ncol;
     ka.tile_cells = (int)tile_cells;
     ka.carry = p->carry;
+    ka.queued = p->queued;
     ka.nang_even = p->ang.n ? (p->ang.n + 1) / 2 : 0;
     for (int k = 0; k < ka.nang_even; ++k) ka.ang_even[k] = p->ang.c[2 * k];
     ka.angmax = p->angmax;

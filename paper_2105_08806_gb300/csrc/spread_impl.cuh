@@ -692,8 +692,8 @@ __device__ __forceinline__ void spread_point_f64(const SpreadArgs &p, const Poin
 // not depend on its warp-mates: bitwise reproducibility across launch shapes; points of 2^29 tile
 // units or more are rare); a lane whose point is below kNegligibleF32 idles.
 template <typename T, int D, int W, typename Tile, bool SLAB>
-__device__ __forceinline__ void spread_point_any(const SpreadArgs &p, const Point<T, D> &pt, const Tile &tile,
-                                                 int row_lo, int nrows, int plane)
+__device__ __forceinline__ void spread_point_body(const SpreadArgs &p, const Point<T, D> &pt, const Tile &tile,
+                                                  int row_lo, int nrows, int plane)
 {
     if constexpr (sizeof(T) == 4) {
         if (fabsf(pt.q) < kIntLimitF32) spread_point_f32<D, W, kInt, SLAB>(p, pt, tile, row_lo, nrows, plane);
@@ -701,6 +701,25 @@ __device__ __forceinline__ void spread_point_any(const SpreadArgs &p, const Poin
     } else {
         spread_point_f64<D, W, SLAB>(p, pt, tile, row_lo, nrows, plane);
     }
+}
+
+template <typename T, int D, int W, typename Tile, bool SLAB>
+__device__ __noinline__ void spread_point_outlined(const SpreadArgs &p, const Point<T, D> &pt, const Tile &tile,
+                                                   int row_lo, int nrows, int plane)
+{
+    spread_point_body<T, D, W, Tile, SLAB>(p, pt, tile, row_lo, nrows, plane);
+}
+
+// 3D points (w^3 taps, two integer kinds) are spread by one out-of-line copy per kernel: inlined
+// at each call site the kernel outgrew the instruction cache (stalls on instruction fetch; 13%
+// longer on the 3D bi-Maxwellian, 70% on 3D BKW once the one-slab queue added a third site).
+// 2D points (w^2 taps) stay inline, where the call's register saves cost 5%.
+template <typename T, int D, int W, typename Tile, bool SLAB>
+__device__ __forceinline__ void spread_point_any(const SpreadArgs &p, const Point<T, D> &pt, const Tile &tile,
+                                                 int row_lo, int nrows, int plane)
+{
+    if constexpr (D == 3) spread_point_outlined<T, D, W, Tile, SLAB>(p, pt, tile, row_lo, nrows, plane);
+    else spread_point_body<T, D, W, Tile, SLAB>(p, pt, tile, row_lo, nrows, plane);
 }
 
 // Advance pr (in steps of `stride`, below `end`) to this lane's next pair that is not negligible:
@@ -816,20 +835,21 @@ __device__ __forceinline__ void queue_get(const T *buf, int slot, Point<T, D> &p
 }
 
 // Spread queue slot `lane` (when valid) with the whole warp.
-template <typename T, int D, int W, typename Tile>
+template <typename T, int D, int W, typename Tile, bool SLAB>
 __device__ __forceinline__ void queue_spread(const SpreadArgs &p, const T *buf, int lane, bool valid,
                                              const Tile &tile, int row_lo, int nrows, int plane)
 {
     if (!valid) return;
     Point<T, D> pt;
     queue_get<T, D>(buf, lane, pt);
-    spread_point_any<T, D, W, Tile, true>(p, pt, tile, row_lo, nrows, plane);
+    spread_point_any<T, D, W, Tile, SLAB>(p, pt, tile, row_lo, nrows, plane);
 }
 
-// The pairs pr = first, first + nthr, ... of one thread, spread into one slab through the
-// warp's queue `buf` (spread_queue_values(d, fp32) x 32 values).  Every loop condition is uniform
-// over the warp.
-template <typename T, int D, int W, typename Tile, bool ANG>
+// The pairs pr = first, first + nthr, ... of one thread, spread through the warp's queue `buf`
+// (spread_queue_values(d, fp32) x 32 values) into one slab (SLAB) or a tile that holds every row;
+// without slabs the queue only leaves out the FP32 points that add exactly zero, so that every
+// lane spreads a real point.  Every loop condition is uniform over the warp.
+template <typename T, int D, int W, typename Tile, bool ANG, bool SLAB = true>
 __device__ __forceinline__ void spread_pairs_queued(const SpreadArgs &p, long long first, long long nthr, T sc, T tau,
                                                     T floor_q, const Tile &tile, int row_lo, int nrows, int plane,
                                                     T *buf)
@@ -850,14 +870,15 @@ __device__ __forceinline__ void spread_pairs_queued(const SpreadArgs &p, long lo
             if (ok) {
                 make_point<T, D, ANG>(p, P, qbase, m, pt);
                 // FP32 points below kNegligibleF32 add exactly zero and are not queued
-                hit = (sizeof(T) == 8 || fabs(pt.q) >= T(kNegligibleF32)) && rows_hit<T, D, W>(p, pt, row_lo, nrows);
+                hit = sizeof(T) == 8 || fabs(pt.q) >= T(kNegligibleF32);
+                if constexpr (SLAB) hit = hit && rows_hit<T, D, W>(p, pt, row_lo, nrows);
             }
             const unsigned mask = __ballot_sync(full, hit);
             const int n = __popc(mask), rank = __popc(mask & lt), room = 32 - count;
             if (hit && rank < room) queue_put<T, D>(buf, count + rank, pt);
             if (n >= room) {  // full: spread 32 points, then queue the rest
                 __syncwarp();
-                queue_spread<T, D, W, Tile>(p, buf, lane, true, tile, row_lo, nrows, plane);
+                queue_spread<T, D, W, Tile, SLAB>(p, buf, lane, true, tile, row_lo, nrows, plane);
                 __syncwarp();
                 if (hit && rank >= room) queue_put<T, D>(buf, rank - room, pt);
                 count = n - room;
@@ -868,7 +889,7 @@ __device__ __forceinline__ void spread_pairs_queued(const SpreadArgs &p, long lo
         if (ok) pr += nthr;
     }
     __syncwarp();
-    queue_spread<T, D, W, Tile>(p, buf, lane, lane < count, tile, row_lo, nrows, plane);
+    queue_spread<T, D, W, Tile, SLAB>(p, buf, lane, lane < count, tile, row_lo, nrows, plane);
 }
 
 struct SlabGeom {
@@ -931,6 +952,11 @@ __global__ void __launch_bounds__(kMaxThreadsF32) k_spread_f32(const __grid_cons
                      (threadIdx.x >> 5) * 32 * spread_queue_values(D, true);
         spread_pairs_queued<float, D, W, SplitTile, ANG>(p, first, nthr, sc, tau, kNegligibleF32, tile, G.row_lo,
                                                           G.nrows, G.plane, buf);
+    } else if (p.queued) {  // one slab: the queues only compact the points that add something
+        float *buf = reinterpret_cast<float *>(smem_raw + (size_t)G.ncell * 4) +
+                     (threadIdx.x >> 5) * 32 * spread_queue_values(D, true);
+        spread_pairs_queued<float, D, W, SplitTile, ANG, false>(p, first, nthr, sc, tau, kNegligibleF32, tile, 0,
+                                                                 G.nrows, G.plane, buf);
     } else {
         spread_pairs<float, D, W, SplitTile, ANG>(p, first, p.npairs, nthr, sc, tau, kNegligibleF32, tile, G.row_lo,
                                                    G.nrows, G.plane);
