@@ -537,7 +537,7 @@ def run_batched(steps, stream, dev, ncells=0, fp64_cells=256):
     return {"cells": len(cells), "ms_per_batch": t, "cell_evals_per_s": len(cells) * 1000.0 / t,
             "points_per_s": info["points"] * 1000.0 / t, "points_per_batch": info["points"],
             "spread_blocks": info["spread_blocks"], "spread_threads": info["spread_threads"],
-            "autotuned": {"threads": tuned[0], "blocks": tuned[1], "ms": tuned[2]},
+            "autotuned": {"threads": tuned[0], "blocks": tuned[1], "item_points": tuned[2], "ms": tuned[3]},
             "one_call_per_cell_ms": t_single[-1], "speedup_vs_one_call_per_cell": t_single[-1] / t,
             "fp64_sample": {"cells": len(sub), "fp32_ms": cmp[PG_PREC_FP32][0], "fp64_ms": cmp[PG_PREC_FP64][0],
                             "speedup_vs_fp64_path": cmp[PG_PREC_FP64][0] / cmp[PG_PREC_FP32][0],

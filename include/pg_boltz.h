@@ -273,16 +273,18 @@ int pg_boltz_batched_use_graph(pg_boltz_plan_t *plan, int enable);
 /*
  * Autotuner of a batched plan's persistent spreading launch (no counterpart in the paper, which
  * evaluates one operator at a time): runs pg_boltz_collide_batched's launch sequence on the
- * caller's f_packed_dev / Q_packed_dev (Q is overwritten) for threads per block in
+ * caller's f_packed_dev / Q_packed_dev (Q is overwritten), first for threads per block in
  * {128, 256, 512, 1024} and every blocks-per-SM count the kernel's occupancy allows (FP32 plans:
- * at most the block count the plan sized its carry counters for), `trials` timed runs each after
- * one warm-up, and keeps the fastest shape for later calls (the next call captures a new graph).
- * The results do not depend on the shape (exact fixed-point sums).  Synchronises the plan's
- * stream.  Optional outputs (host): threads per block, blocks, best time in ms of one call.
+ * at most the block count the plan sized its carry counters for), then at the fastest shape for
+ * work items of 2^15, 2^16, ..., 2^19 points (the node-pair ranges the blocks take from the
+ * global counter); `trials` timed runs each after one warm-up.  Keeps the fastest shape and item
+ * size for later calls (the next call captures a new graph).  The results do not depend on
+ * either (exact fixed-point sums).  Synchronises the plan's stream.  Optional outputs (host):
+ * threads per block, blocks, points per work item, best time in ms of one call.
  * PG_ERR_ARG for NULL or overlapping arrays or trials outside [1, 100]; PG_ERR_STATE on plain plans.
  */
 int pg_boltz_batched_autotune(pg_boltz_plan_t *plan, const double *f_packed_dev, double *Q_packed_dev, int trials,
-                              int *threads_out, int *blocks_out, double *ms_out);
+                              int *threads_out, int *blocks_out, long long *item_points_out, double *ms_out);
 
 /*
  * Measured throughput (atomic additions per second, whole GPU) of 32-bit integer atomic adds

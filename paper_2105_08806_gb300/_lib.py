@@ -103,7 +103,7 @@ def lib():
     L.pg_boltz_batched_offsets.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.pg_boltz_batched_offsets.restype = ctypes.c_int
     L.pg_boltz_batched_use_graph.argtypes = [vp, ctypes.c_int]
-    L.pg_boltz_batched_autotune.argtypes = [vp, vp, vp, ctypes.c_int, ip, ip, dp]
+    L.pg_boltz_batched_autotune.argtypes = [vp, vp, vp, ctypes.c_int, ip, ip, ctypes.POINTER(ctypes.c_longlong), dp]
     L.pg_boltz_batched_use_graph.restype = ctypes.c_int
     L.pg_boltz_conservation.argtypes = [vp, vp, dp]
     L.pg_boltz_conservation.restype = ctypes.c_int
@@ -316,11 +316,13 @@ class BatchedPlan(Plan):
         _check(lib().pg_boltz_collide_batched(self._h, ctypes.c_void_p(_ptr(f)), ctypes.c_void_p(_ptr(Q))))
 
     def autotune(self, f, Q, trials=2):
-        """Time the spreading launch shapes on (f, Q) and keep the fastest; returns (threads, blocks, ms)."""
-        thr, blk, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+        """Time the spreading launch shapes, then the work-item sizes, on (f, Q) and keep the fastest;
+        returns (threads, blocks, item_points, ms)."""
+        thr, blk, items, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_longlong(0), ctypes.c_double(0.0)
         _check(lib().pg_boltz_batched_autotune(self._h, ctypes.c_void_p(_ptr(f)), ctypes.c_void_p(_ptr(Q)), int(trials),
-                                               ctypes.byref(thr), ctypes.byref(blk), ctypes.byref(ms)))
-        return thr.value, blk.value, ms.value
+                                               ctypes.byref(thr), ctypes.byref(blk), ctypes.byref(items),
+                                               ctypes.byref(ms)))
+        return thr.value, blk.value, items.value, ms.value
 
     def use_graph(self, enable: bool):
         _check(lib().pg_boltz_batched_use_graph(self._h, int(bool(enable))))

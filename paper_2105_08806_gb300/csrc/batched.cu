@@ -63,6 +63,7 @@ struct BatchArgs {
     unsigned long long *grid;
     int *carry;          // FP32: per-block carry counters, blocks x carry_stride
     int carry_stride;    // cells of the largest cell tile
+    int queue_off;       // FP32: byte offset of the warps' point queues in dynamic shared memory
     double *scratch;
     const double *v64;
     const float *v32;
@@ -395,10 +396,13 @@ __global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __gr
         const long long p0 = (long long)(item - s_cd.item0) * s_cd.chunk;
         const long long p1 = min(p0 + (long long)s_cd.chunk, s_cd.pairs);
         const long long first = p0 + (long long)lane * nwarp + warp;
-        if constexpr (F32)
-            spread_pairs<T, D, W, SplitTile, false>(sa, first, p1, blockDim.x, sc, tau, floor_q, SplitTile{lo, carry}, 0,
-                                                     s_cd.nf, plane);
-        else
+        if constexpr (F32) {
+            // the warp's queue compacts the points that add something (FP32 points below 0.1 tile
+            // unit add exactly zero), so that every lane spreads a real point
+            float *buf = reinterpret_cast<float *>(smem_raw + b.queue_off) + warp * 32 * spread_queue_values(D, true);
+            spread_pairs_queued<T, D, W, SplitTile, false, false>(sa, first, p1, blockDim.x, sc, tau, floor_q,
+                                                                   SplitTile{lo, carry}, 0, s_cd.nf, plane, buf);
+        } else
             spread_pairs<T, D, W, DoubleTile, false>(sa, first, p1, blockDim.x, sc, tau, floor_q, DoubleTile{dv}, 0,
                                                       s_cd.nf, plane);
         __syncthreads();
@@ -539,6 +543,13 @@ struct BatchState {
     int nitems = 0;
     int spread_blocks = 0, spread_threads = 0;
     size_t spread_smem = 0;
+    size_t tile_smem = 0;    // dynamic shared memory of the largest cell tile (16-byte multiple)
+    size_t static_smem = 0;  // the spreading kernel's static shared memory
+    std::vector<pgb::CellDesc> cells;  // host copy of the cell descriptors (work items change)
+    pgb::CellDesc *d_cells = nullptr;
+    int *d_items = nullptr;   // cell of each work item
+    int item_capacity = 0;    // work items d_items holds (the smallest item size's count)
+    long long item_points = 0;  // points per work item
     int carry_blocks = 0;  // blocks the FP32 carry-counter array was sized for
     pgb::BatchArgs args{};
     bool use_graph = true;
@@ -564,7 +575,34 @@ void pg_free_batch(BatchState *b)
 
 namespace {
 
-constexpr long long kItemPoints = 1 << 17;  // points per work item
+constexpr long long kItemPoints = 1 << 17;     // points per work item (default)
+constexpr long long kItemPointsMin = 1 << 15;  // the autotuner's work-item sizes: 2^15 .. 2^19
+constexpr long long kItemPointsMax = 1 << 19;
+
+// Split every cell's node pairs into work items of about item_points points (at least 64 pairs):
+// sets each cell's chunk and first item; item_cell (optional) receives the cell of every item.
+// Returns the number of items.
+long long split_items(std::vector<pgb::CellDesc> &cells, long long item_points, std::vector<int> *item_cell)
+{
+    long long n = 0;
+    if (item_cell) item_cell->clear();
+    for (size_t c = 0; c < cells.size(); ++c) {
+        pgb::CellDesc &cd = cells[c];
+        cd.chunk = (int)std::max<long long>(64, item_points / cd.M);
+        cd.item0 = (int)n;
+        const long long nitem = (cd.pairs + cd.chunk - 1) / cd.chunk;
+        if (item_cell) item_cell->insert(item_cell->end(), (size_t)nitem, (int)c);
+        n += nitem;
+    }
+    return n;
+}
+
+// Dynamic shared memory of a spreading launch with `threads` threads: the largest cell's tile,
+// then (FP32) one point queue per warp.
+size_t batch_smem(const BatchState &B, int threads)
+{
+    return B.tile_smem + (B.prec == PG_PREC_FP32 ? pgb::spread_queue_bytes(threads, B.d, true) : 0);
+}
 
 int enqueue_batch(pg_boltz_plan_t *p, cudaStream_t s, const double *f, double *Q)
 {
@@ -725,14 +763,20 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
         cd.s_len = std::max<long long>(modes, (long long)(N + 1) * (long long)ipow(cd.nf, d - 1));
         cd.s_off = s_off;
         s_off += 4 * cd.s_len;
-        cd.chunk = (int)std::max<long long>(64, kItemPoints / M);
-        cd.item0 = (int)item_cell.size();
-        const long long nitem = (cd.pairs + cd.chunk - 1) / cd.chunk;
-        for (long long t = 0; t < nitem; ++t) item_cell.push_back(c);
         B->points += cd.pairs * M;
         B->pairs += cd.pairs;
     }
     B->offsets[ncell] = f_off;
+    // work items: room for the autotuner's smallest item size, the default size to start with
+    const long long capacity = split_items(cells, kItemPointsMin, nullptr);
+    if (capacity > (1ll << 30)) {
+        set_error(PG_ERR_ARG, "batched plan: too many work items (%lld)", capacity);
+        free_plan(p);
+        return nullptr;
+    }
+    B->item_capacity = (int)capacity;
+    B->item_points = kItemPoints;
+    split_items(cells, kItemPoints, &item_cell);
     B->nitems = (int)item_cell.size();
     B->grid_cells = grid_off;
     std::vector<float> v32(v64.begin(), v64.end()), sig32(sig64.begin(), sig64.end()), wsig32(wsig64.begin(), wsig64.end());
@@ -757,7 +801,9 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
     std::vector<double> kpoly(pgb::kPolyCoefF64, 0.0);
     kernel_poly(B->w, B->beta, kpoly.data());
     // each failing call has recorded its error for pg_boltz_last_error
-    if (upload(p, &d_cells, cells) || upload(p, &d_kp, kpoly) || upload(p, &d_items, item_cell) ||
+    std::vector<int> items_room(item_cell);  // the item array has room for the smallest item size
+    items_room.resize((size_t)B->item_capacity, 0);
+    if (upload(p, &d_cells, cells) || upload(p, &d_kp, kpoly) || upload(p, &d_items, items_room) ||
         upload(p, &d_v64, v64) || upload(p, &d_v32, v32) || upload(p, &d_v32lo, v32lo) || upload(p, &d_sa, scale_a) ||
         upload(p, &d_im, inv_mu2) ||
         upload(p, &d_R, R) || upload(p, &d_E, E) || upload(p, &d_D, D) || upload(p, &d_s64, sig64) ||
@@ -771,6 +817,9 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
     }
     a.cells = d_cells;
     a.item_cell = d_items;
+    B->cells = cells;
+    B->d_cells = d_cells;
+    B->d_items = d_items;
     a.counter = static_cast<int *>(counter_grid);
     a.grid = reinterpret_cast<unsigned long long *>(static_cast<char *>(counter_grid) + 256);
     a.v64 = d_v64;
@@ -794,19 +843,21 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
         free_plan(p);
         return nullptr;
     }
-    B->spread_smem = (size_t)max_cells_tile * (f32 ? 4 : 8);  // FP32: one word per cell; FP64: a double
+    // FP32: one word per cell; FP64: a double
+    B->tile_smem = ((size_t)max_cells_tile * (f32 ? 4 : 8) + 15) / 16 * 16;
+    a.queue_off = (int)B->tile_smem;
     // the kernel's static shared memory: the current cell's descriptor and spreading arguments,
     // FP64: the kernel polynomial
-    const size_t static_smem =
+    B->static_smem =
         sizeof(pgb::CellDesc) + sizeof(pgb::SpreadArgs) + 64 + (f32 ? 0 : sizeof(double) * pgb::kPolyCoefF64);
-    if (B->spread_smem + static_smem > prop.sharedMemPerBlockOptin) {
+    const size_t per_block_extra = B->static_smem + 1024 + prop.reservedSharedMemPerBlock;
+    if (batch_smem(*B, 128) + B->static_smem > prop.sharedMemPerBlockOptin) {
         set_error(PG_ERR_ARG, "largest cell's folded grid (%d cells) does not fit shared memory", max_cells_tile);
         free_plan(p);
         return nullptr;
     }
     const int max_threads = f32 ? pgb::kBatchThreadsF32 : pgb::kMaxThreadsF64;
-    int per_sm = (int)(prop.sharedMemPerMultiprocessor /
-                       (B->spread_smem + static_smem + 1024 + prop.reservedSharedMemPerBlock));
+    int per_sm = (int)(prop.sharedMemPerMultiprocessor / (batch_smem(*B, 128) + per_block_extra));
     per_sm = std::max(per_sm, 1);
     if (o.spread_blocks_per_sm > 0) per_sm = std::min(per_sm, o.spread_blocks_per_sm);
     B->spread_threads = (o.spread_threads > 0) ? o.spread_threads
@@ -816,7 +867,15 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
         free_plan(p);
         return nullptr;
     }
+    B->spread_smem = batch_smem(*B, B->spread_threads);
+    if (B->spread_smem + B->static_smem > prop.sharedMemPerBlockOptin) {
+        set_error(PG_ERR_ARG, "largest cell's folded grid (%d cells) and the queues of %d threads do not fit "
+                  "shared memory", max_cells_tile, B->spread_threads);
+        free_plan(p);
+        return nullptr;
+    }
     per_sm = std::min(per_sm, std::max(1, prop.maxThreadsPerMultiProcessor / B->spread_threads));
+    per_sm = std::min(per_sm, std::max(1, (int)(prop.sharedMemPerMultiprocessor / (B->spread_smem + per_block_extra))));
     B->spread_blocks = prop.multiProcessorCount * per_sm;
     a.carry = nullptr;
     a.carry_stride = max_cells_tile;
@@ -825,7 +884,9 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
         free_plan(p);
         return nullptr;
     }
-    if (cuda_check(pgb::batch_spread_attr(f32, d, B->w, B->spread_smem), "batched spread attribute")) {
+    // the attribute covers every launch shape the autotuner may try
+    const size_t smem_attr = std::min(batch_smem(*B, max_threads), prop.sharedMemPerBlockOptin - B->static_smem);
+    if (cuda_check(pgb::batch_spread_attr(f32, d, B->w, smem_attr), "batched spread attribute")) {
         free_plan(p);
         return nullptr;
     }
@@ -937,8 +998,33 @@ PG_API int pg_boltz_batched_use_graph(pg_boltz_plan_t *p, int enable)
 // fastest: threads per block in {128, 256, 512, 1024} (within the kernel's bound) and every
 // blocks-per-SM count the kernel's occupancy allows, up to the blocks the carry counters were
 // sized for.  Each shape: one launch sequence to warm up, then the best of `trials` timed ones.
+namespace {
+
+// Re-split the cells into work items of about item_points points and upload the new item table
+// (synchronises the plan's stream: the host tables are temporaries).
+int apply_item_points(pg_boltz_plan_t *p, long long item_points)
+{
+    BatchState &B = *p->batch;
+    std::vector<int> item_cell;
+    const long long n = split_items(B.cells, item_points, &item_cell);
+    if (n > B.item_capacity) return set_error(PG_ERR_STATE, "work items exceed the plan's item table");
+    int rc;
+    if ((rc = cuda_check(cudaMemcpyAsync(B.d_cells, B.cells.data(), B.cells.size() * sizeof(pgb::CellDesc),
+                                         cudaMemcpyHostToDevice, p->stream), "upload cells")) ||
+        (rc = cuda_check(cudaMemcpyAsync(B.d_items, item_cell.data(), (size_t)n * sizeof(int),
+                                         cudaMemcpyHostToDevice, p->stream), "upload work items")) ||
+        (rc = cuda_check(cudaStreamSynchronize(p->stream), "stream sync")))
+        return rc;
+    B.nitems = (int)n;
+    B.args.nitems = (int)n;
+    B.item_points = item_points;
+    return PG_OK;
+}
+
+}  // namespace
+
 PG_API int pg_boltz_batched_autotune(pg_boltz_plan_t *p, const double *f_dev, double *Q_dev, int trials,
-                                     int *threads_out, int *blocks_out, double *ms_out)
+                                     int *threads_out, int *blocks_out, long long *item_points_out, double *ms_out)
 {
     if (!p) return set_error(PG_ERR_ARG, "plan is NULL");
     if (!p->batch) return set_error(PG_ERR_STATE, "pg_boltz_batched_autotune needs a batched plan");
@@ -957,31 +1043,43 @@ PG_API int pg_boltz_batched_autotune(pg_boltz_plan_t *p, const double *f_dev, do
     const bool f32 = (B.prec == PG_PREC_FP32);
     const int max_threads = f32 ? pgb::kBatchThreadsF32 : pgb::kMaxThreadsF64;
     const int best0_threads = B.spread_threads, best0_blocks = B.spread_blocks;
+    const long long best0_items = B.item_points;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if ((rc = cuda_check(cudaEventCreate(&e0), "event")) || (rc = cuda_check(cudaEventCreate(&e1), "event"))) {
         if (e0) cudaEventDestroy(e0);
         return rc;
     }
+    // best of `trials` timed runs of the current configuration after one warm-up
+    auto time_config = [&](double &ms_best) -> int {
+        ms_best = 1e300;
+        int r = PG_OK;
+        for (int t = 0; t <= trials && r == PG_OK; ++t) {
+            if ((r = cuda_check(cudaEventRecord(e0, p->stream), "event record"))) break;
+            if ((r = enqueue_batch(p, p->stream, f_dev, Q_dev))) break;
+            if ((r = cuda_check(cudaEventRecord(e1, p->stream), "event record"))) break;
+            if ((r = cuda_check(cudaEventSynchronize(e1), "event sync"))) break;
+            float ms = 0.0f;
+            if ((r = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "elapsed"))) break;
+            if (t > 0) ms_best = std::min(ms_best, (double)ms);  // t = 0 warms up
+        }
+        return r;
+    };
+    // 1. launch shapes at the current work-item size
     int best_threads = best0_threads, best_blocks = best0_blocks;
     double best_ms = 1e300;
     for (int threads = 128; threads <= max_threads && rc == PG_OK; threads *= 2) {
         int occ = 0;
-        if (pgb::batch_spread_occupancy(f32, B.d, B.w, threads, B.spread_smem, &occ) != cudaSuccess || occ < 1) continue;
+        const size_t smem = batch_smem(B, threads);
+        if (smem + B.static_smem > prop.sharedMemPerBlockOptin) continue;
+        if (pgb::batch_spread_occupancy(f32, B.d, B.w, threads, smem, &occ) != cudaSuccess || occ < 1) continue;
         for (int per_sm = 1; per_sm <= occ && rc == PG_OK; ++per_sm) {
             const int blocks = prop.multiProcessorCount * per_sm;
             if (f32 && blocks > B.carry_blocks) break;  // no carry counters for more blocks
             B.spread_threads = threads;
             B.spread_blocks = blocks;
+            B.spread_smem = smem;
             double ms_best = 1e300;
-            for (int t = 0; t <= trials && rc == PG_OK; ++t) {
-                if ((rc = cuda_check(cudaEventRecord(e0, p->stream), "event record"))) break;
-                if ((rc = enqueue_batch(p, p->stream, f_dev, Q_dev))) break;
-                if ((rc = cuda_check(cudaEventRecord(e1, p->stream), "event record"))) break;
-                if ((rc = cuda_check(cudaEventSynchronize(e1), "event sync"))) break;
-                float ms = 0.0f;
-                if ((rc = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "elapsed"))) break;
-                if (t > 0) ms_best = std::min(ms_best, (double)ms);  // t = 0 warms up
-            }
+            rc = time_config(ms_best);
             if (rc == PG_OK && ms_best < best_ms) {
                 best_ms = ms_best;
                 best_threads = threads;
@@ -989,11 +1087,29 @@ PG_API int pg_boltz_batched_autotune(pg_boltz_plan_t *p, const double *f_dev, do
             }
         }
     }
+    // 2. work-item sizes at the best shape
+    long long best_items = B.item_points;
+    if (rc == PG_OK) {
+        B.spread_threads = best_threads;
+        B.spread_blocks = best_blocks;
+        B.spread_smem = batch_smem(B, best_threads);
+        for (long long ip = kItemPointsMin; ip <= kItemPointsMax && rc == PG_OK; ip *= 2) {
+            if (ip == best_items) continue;  // timed in step 1
+            double ms_best = 1e300;
+            if ((rc = apply_item_points(p, ip)) || (rc = time_config(ms_best))) break;
+            if (ms_best < best_ms) {
+                best_ms = ms_best;
+                best_items = ip;
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     B.spread_threads = (rc == PG_OK) ? best_threads : best0_threads;
     B.spread_blocks = (rc == PG_OK) ? best_blocks : best0_blocks;
-    // the captured graph holds the old launch shape: capture again on the next call
+    B.spread_smem = batch_smem(B, B.spread_threads);
+    const int rc_items = apply_item_points(p, (rc == PG_OK) ? best_items : best0_items);
+    // the captured graph holds the old launch shape and item count: capture again on the next call
     if (B.exec) {
         cudaGraphExecDestroy(B.exec);
         B.exec = nullptr;
@@ -1003,10 +1119,13 @@ PG_API int pg_boltz_batched_autotune(pg_boltz_plan_t *p, const double *f_dev, do
         B.graph = nullptr;
     }
     if (rc) return rc;
+    if (rc_items) return rc_items;
     p->info.spread_threads = B.spread_threads;
     p->info.spread_blocks = B.spread_blocks;
+    p->info.spread_smem_bytes = B.spread_smem;
     if (threads_out) *threads_out = B.spread_threads;
     if (blocks_out) *blocks_out = B.spread_blocks;
+    if (item_points_out) *item_points_out = B.item_points;
     if (ms_out) *ms_out = best_ms;
     return PG_OK;
 }

@@ -845,14 +845,14 @@ __device__ __forceinline__ void queue_spread(const SpreadArgs &p, const T *buf, 
     spread_point_any<T, D, W, Tile, SLAB>(p, pt, tile, row_lo, nrows, plane);
 }
 
-// The pairs pr = first, first + nthr, ... of one thread, spread through the warp's queue `buf`
-// (spread_queue_values(d, fp32) x 32 values) into one slab (SLAB) or a tile that holds every row;
-// without slabs the queue only leaves out the FP32 points that add exactly zero, so that every
-// lane spreads a real point.  Every loop condition is uniform over the warp.
+// The pairs pr = first, first + nthr, ... below end of one thread, spread through the warp's
+// queue `buf` (spread_queue_values(d, fp32) x 32 values) into one slab (SLAB) or a tile that
+// holds every row; without slabs the queue only leaves out the FP32 points that add exactly zero,
+// so that every lane spreads a real point.  Every loop condition is uniform over the warp.
 template <typename T, int D, int W, typename Tile, bool ANG, bool SLAB = true>
-__device__ __forceinline__ void spread_pairs_queued(const SpreadArgs &p, long long first, long long nthr, T sc, T tau,
-                                                    T floor_q, const Tile &tile, int row_lo, int nrows, int plane,
-                                                    T *buf)
+__device__ __forceinline__ void spread_pairs_queued(const SpreadArgs &p, long long first, long long end,
+                                                    long long nthr, T sc, T tau, T floor_q, const Tile &tile,
+                                                    int row_lo, int nrows, int plane, T *buf)
 {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -861,7 +861,7 @@ __device__ __forceinline__ void spread_pairs_queued(const SpreadArgs &p, long lo
     long long pr = first;
     for (;;) {
         PairData<T, D> P;
-        const bool ok = next_pair<T, D, ANG>(p, pr, p.npairs, nthr, sc, tau, floor_q, P);
+        const bool ok = next_pair<T, D, ANG>(p, pr, end, nthr, sc, tau, floor_q, P);
         if (!__any_sync(full, ok)) break;
         const T qbase = ok ? P.base * sc : T(0);
         for (int m = 0; m < p.M; ++m) {
@@ -950,13 +950,13 @@ __global__ void __launch_bounds__(kMaxThreadsF32) k_spread_f32(const __grid_cons
     if (p.nslab > 1) {
         float *buf = reinterpret_cast<float *>(smem_raw + (size_t)p.rows_per_slab * G.plane * 4) +
                      (threadIdx.x >> 5) * 32 * spread_queue_values(D, true);
-        spread_pairs_queued<float, D, W, SplitTile, ANG>(p, first, nthr, sc, tau, kNegligibleF32, tile, G.row_lo,
-                                                          G.nrows, G.plane, buf);
+        spread_pairs_queued<float, D, W, SplitTile, ANG>(p, first, p.npairs, nthr, sc, tau, kNegligibleF32, tile,
+                                                          G.row_lo, G.nrows, G.plane, buf);
     } else if (p.queued) {  // one slab: the queues only compact the points that add something
         float *buf = reinterpret_cast<float *>(smem_raw + (size_t)G.ncell * 4) +
                      (threadIdx.x >> 5) * 32 * spread_queue_values(D, true);
-        spread_pairs_queued<float, D, W, SplitTile, ANG, false>(p, first, nthr, sc, tau, kNegligibleF32, tile, 0,
-                                                                 G.nrows, G.plane, buf);
+        spread_pairs_queued<float, D, W, SplitTile, ANG, false>(p, first, p.npairs, nthr, sc, tau, kNegligibleF32,
+                                                                 tile, 0, G.nrows, G.plane, buf);
     } else {
         spread_pairs<float, D, W, SplitTile, ANG>(p, first, p.npairs, nthr, sc, tau, kNegligibleF32, tile, G.row_lo,
                                                    G.nrows, G.plane);
@@ -992,8 +992,8 @@ __global__ void __launch_bounds__(kMaxThreadsF64) k_spread_f64(const __grid_cons
     if (p.nslab > 1) {
         double *buf = reinterpret_cast<double *>(smem_raw + (size_t)p.rows_per_slab * G.plane * 8) +
                       (threadIdx.x >> 5) * 32 * spread_queue_values(D, false);
-        spread_pairs_queued<double, D, W, DoubleTile, ANG>(p, first, nthr, 1.0, tau, floor_q, tile, G.row_lo, G.nrows,
-                                                            G.plane, buf);
+        spread_pairs_queued<double, D, W, DoubleTile, ANG>(p, first, p.npairs, nthr, 1.0, tau, floor_q, tile,
+                                                            G.row_lo, G.nrows, G.plane, buf);
     } else {
         spread_pairs<double, D, W, DoubleTile, ANG>(p, first, p.npairs, nthr, 1.0, tau, floor_q, tile, G.row_lo,
                                                      G.nrows, G.plane);

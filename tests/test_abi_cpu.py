@@ -61,7 +61,7 @@ def test_null_handles(L):
     assert L.pg_boltz_info(None, None) == _lib.PG_ERR_ARG
     assert L.pg_boltz_set_stream(None, None) == _lib.PG_ERR_ARG
     assert L.pg_boltz_evaluate(None, None, 1, None, None) == _lib.PG_ERR_ARG
-    assert L.pg_boltz_batched_autotune(None, None, None, 2, None, None, None) == _lib.PG_ERR_ARG
+    assert L.pg_boltz_batched_autotune(None, None, None, 2, None, None, None, None) == _lib.PG_ERR_ARG
     L.pg_boltz_destroy(None)  # NULL-safe
 
 

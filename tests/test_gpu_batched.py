@@ -150,9 +150,9 @@ def test_batched_screened_matches_oracle():
 
 
 def test_autotune_keeps_results_bitwise():
-    """pg_boltz_batched_autotune times the persistent kernel's launch shapes on the caller's data
-    and keeps the fastest; the fixed-point sums do not depend on the shape, so the results before
-    and after tuning are identical, and the graph captured afterwards uses the new shape."""
+    """pg_boltz_batched_autotune times the persistent kernel's launch shapes and work-item sizes on
+    the caller's data and keeps the fastest; the fixed-point sums depend on neither, so the results
+    before and after tuning are identical, and the graph captured afterwards uses the new shape."""
     import torch
     from paper_2105_08806_gb300 import BatchedPlan
     d = 2
@@ -163,13 +163,14 @@ def test_autotune_keeps_results_bitwise():
         Q1 = torch.empty_like(f)
         bp.collide(f, Q1)
         Q2 = torch.empty_like(f)
-        thr, blocks, ms = bp.autotune(f, Q2, trials=1)
+        thr, blocks, items, ms = bp.autotune(f, Q2, trials=1)
         Q3 = torch.empty_like(f)
         bp.collide(f, Q3)
         torch.cuda.synchronize()
         info = bp.info()
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     assert thr in (128, 256, 512, 1024) and blocks % sms == 0 and ms > 0
+    assert items in (2 ** 15, 2 ** 16, 2 ** 17, 2 ** 18, 2 ** 19)
     assert (info["spread_threads"], info["spread_blocks"]) == (thr, blocks)
     assert torch.equal(Q1, Q2) and torch.equal(Q1, Q3)
 
