@@ -316,13 +316,14 @@ __device__ __forceinline__ void cell_args(const BatchArgs &b, const CellDesc &cd
     fill_spread_consts(sa);
 }
 
-template <typename T>
-constexpr int max_threads_of() { return sizeof(T) == 4 ? kBatchThreadsF32 : kMaxThreadsF64; }
+template <typename T, int D>
+constexpr int max_threads_of() { return sizeof(T) == 4 ? kBatchThreadsF32 : max_threads_f64(D); }
 
 // Add a cell's block tile to the cell's global grid (padding columns folded onto their cells).
 template <bool F32, int D>
-__device__ __forceinline__ void batch_flush(const int *lo, const int *carry, const double *dv, int ncell, int nf,
-                                            int ncol, int cpad, int n, unsigned long long *grid, int shift, int Eg)
+__device__ __forceinline__ void batch_flush(const int *lo, const int *carry, const spread_detail::WideTile &wt,
+                                            int ncell, int nf, int ncol, int cpad, int n, unsigned long long *grid,
+                                            int shift)
 {
     for (int e = threadIdx.x; e < ncell; e += blockDim.x) {
         const int gc = spread_detail::tile_to_grid_cell(e, D, nf, ncol, cpad, n, 0);
@@ -330,14 +331,14 @@ __device__ __forceinline__ void batch_flush(const int *lo, const int *carry, con
             const long long v = (long long)carry[e] * 4294967296LL + lo[e];
             if (v) atomicAdd(grid + gc, (unsigned long long)(v * (1ll << shift)));
         } else {
-            const long long v = __double2ll_rn(dv[e] * ldexp(1.0, Eg));
+            const long long v = wt.value(e);  // grid units
             if (v) atomicAdd(grid + gc, (unsigned long long)v);
         }
     }
 }
 
 template <typename T, int D, int W>
-__global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __grid_constant__ BatchArgs b)
+__global__ void __launch_bounds__(max_threads_of<T, D>(), 1) k_batch_spread(const __grid_constant__ BatchArgs b)
 {
     using namespace spread_detail;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -353,7 +354,9 @@ __global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __gr
     if constexpr (!F32) load_kernel_poly(b.kpoly);  // the same kernel polynomial for every cell
     int *lo = reinterpret_cast<int *>(smem_raw);
     int *carry = F32 ? b.carry + (size_t)blockIdx.x * b.carry_stride : nullptr;
-    double *dv = reinterpret_cast<double *>(smem_raw);
+    // FP64: fraction, low and high words of the largest cell tile (carry_stride cells)
+    unsigned *words = reinterpret_cast<unsigned *>(smem_raw);
+    const WideTile wt{words, words + b.carry_stride, reinterpret_cast<int *>(words + 2 * b.carry_stride)};
     // add the current cell's tile to its grid (padding columns folded onto their cells)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (;;) {
@@ -364,7 +367,7 @@ __global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __gr
         const int cell = b.item_cell[item];
         if (cell != cur) {
             if (cur >= 0)  // the previous cell's tile
-                batch_flush<F32, D>(lo, carry, dv, ncell, s_cd.nf, sa.ncol, sa.cpad, s_cd.n, sa.grid, shift, Eg);
+                batch_flush<F32, D>(lo, carry, wt, ncell, s_cd.nf, sa.ncol, sa.cpad, s_cd.n, sa.grid, shift);
             __syncthreads();
             if (threadIdx.x == 0) s_cd = b.cells[cell];
             __syncthreads();
@@ -377,17 +380,20 @@ __global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __gr
             Eg = global_exponent(Bc);
             const int Et = F32 ? min(Eg - tile_bits(D), 120) : Eg;
             shift = Eg - Et;
-            sc = F32 ? T(ldexp(1.0, Et)) : T(1);
+            sc = T(ldexp(1.0, Et));  // strengths in tile units (FP64: grid units, Et = Eg)
             tau = T(b.Tcell[cell]);
-            // negligible pairs: FP32 points below 0.1 tile unit add exactly zero; FP64 pairs whose
-            // summed bounds stay below 2^-64 B
-            floor_q = F32 ? T(spread_detail::kNegligibleF32) : T(ldexp(Bc, -64) * sa.cd.wmax / (double)s_cd.pairs);
+            // negligible points: FP32 points below 0.1 tile unit add exactly zero; FP64 pairs whose
+            // summed bounds stay below 2^-64 B are skipped
+            floor_q = F32 ? T(spread_detail::kNegligibleF32)
+                          : T(ldexp(Bc, Eg - 64) * sa.cd.wmax / (double)s_cd.pairs);
             for (int e = threadIdx.x; e < ncell; e += blockDim.x) {
                 if constexpr (F32) {
                     lo[e] = 0;
                     carry[e] = 0;
                 } else {
-                    dv[e] = 0.0;
+                    wt.fr[e] = 0u;
+                    wt.lo[e] = 0u;
+                    wt.hi[e] = 0;
                 }
             }
             __syncthreads();
@@ -403,11 +409,11 @@ __global__ void __launch_bounds__(max_threads_of<T>()) k_batch_spread(const __gr
             spread_pairs_queued<T, D, W, SplitTile, false, false>(sa, first, p1, blockDim.x, sc, tau, floor_q,
                                                                    SplitTile{lo, carry}, 0, s_cd.nf, plane, buf);
         } else
-            spread_pairs<T, D, W, DoubleTile, false>(sa, first, p1, blockDim.x, sc, tau, floor_q, DoubleTile{dv}, 0,
+            spread_pairs<T, D, W, WideTile, false>(sa, first, p1, blockDim.x, sc, tau, floor_q, wt, 0,
                                                       s_cd.nf, plane);
         __syncthreads();
     }
-    if (cur >= 0) batch_flush<F32, D>(lo, carry, dv, ncell, s_cd.nf, sa.ncol, sa.cpad, s_cd.n, sa.grid, shift, Eg);
+    if (cur >= 0) batch_flush<F32, D>(lo, carry, wt, ncell, s_cd.nf, sa.ncol, sa.cpad, s_cd.n, sa.grid, shift);
 }
 
 // One block per cell: Q = D(grid) - E(h) along every axis (Section 4.2).
@@ -843,8 +849,8 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
         free_plan(p);
         return nullptr;
     }
-    // FP32: one word per cell; FP64: a double
-    B->tile_smem = ((size_t)max_cells_tile * (f32 ? 4 : 8) + 15) / 16 * 16;
+    // FP32: one 32-bit word per cell; FP64: three
+    B->tile_smem = pgb::tile_bytes((size_t)max_cells_tile, f32);
     a.queue_off = (int)B->tile_smem;
     // the kernel's static shared memory: the current cell's descriptor and spreading arguments,
     // FP64: the kernel polynomial
@@ -856,7 +862,7 @@ PG_API pg_boltz_plan_t *pg_boltz_plan_batched_ex(const pg_boltz_opts_t *opts, in
         free_plan(p);
         return nullptr;
     }
-    const int max_threads = f32 ? pgb::kBatchThreadsF32 : pgb::kMaxThreadsF64;
+    const int max_threads = f32 ? pgb::kBatchThreadsF32 : pgb::max_threads_f64(B->d);
     int per_sm = (int)(prop.sharedMemPerMultiprocessor / (batch_smem(*B, 128) + per_block_extra));
     per_sm = std::max(per_sm, 1);
     if (o.spread_blocks_per_sm > 0) per_sm = std::min(per_sm, o.spread_blocks_per_sm);
@@ -1041,7 +1047,7 @@ PG_API int pg_boltz_batched_autotune(pg_boltz_plan_t *p, const double *f_dev, do
     int rc = cuda_check(cudaGetDeviceProperties(&prop, p->device), "cudaGetDeviceProperties");
     if (rc) return rc;
     const bool f32 = (B.prec == PG_PREC_FP32);
-    const int max_threads = f32 ? pgb::kBatchThreadsF32 : pgb::kMaxThreadsF64;
+    const int max_threads = f32 ? pgb::kBatchThreadsF32 : pgb::max_threads_f64(B.d);
     const int best0_threads = B.spread_threads, best0_blocks = B.spread_blocks;
     const long long best0_items = B.item_points;
     cudaEvent_t e0 = nullptr, e1 = nullptr;

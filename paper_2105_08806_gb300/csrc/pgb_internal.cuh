@@ -130,6 +130,12 @@ __host__ __device__ inline size_t spread_queue_bytes(int threads, int d, bool f3
 {
     return (size_t)(threads / 32) * 32 * spread_queue_values(d, f32) * (f32 ? 4 : 8);
 }
+// Shared memory of a block tile of `cells` cells, rounded up to 16 bytes (the queues follow it):
+// FP32 tiles hold one 32-bit word per cell, FP64 tiles three (fraction, low and high words).
+__host__ __device__ inline size_t tile_bytes(size_t cells, bool f32)
+{
+    return (cells * (f32 ? 4 : 12) + 15) / 16 * 16;
+}
 
 // Padding columns of the block tiles' last axis for kernel width w: the unfolded support of a point
 // at grid coordinate x in [0, n/2] spans floor(x - w/2) + 1 .. floor(x + w/2), i.e. at most w/2
@@ -177,7 +183,10 @@ static_assert(kPolyCoefF64 >= ((kMaxWidthF64 + 1) / 2) * kernel_poly_terms(kMaxW
 constexpr int kMinWidth = 2;
 // Largest spreading block for each type (the kernels' launch bounds).
 constexpr int kMaxThreadsF32 = 1024;
-constexpr int kMaxThreadsF64 = 256;
+// FP64: 2D kernels use up to 255 registers per thread, 3D kernels fit 128 (their per-point
+// spreading is out of line), so 3D blocks hold twice the threads (integer shared atomics whose
+// returned values feed the next step want many resident warps).
+__host__ __device__ constexpr int max_threads_f64(int d) { return d == 3 ? 512 : 256; }
 // Largest block of the batched FP32 spreading kernel.
 constexpr int kBatchThreadsF32 = 1024;
 

@@ -112,14 +112,15 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
     cudaDeviceProp prop;
     cudaError_t e = cudaGetDeviceProperties(&prop, p->device);
     if (e != cudaSuccess) return set_error(PG_ERR_CUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e));
-    const size_t elem = (p->prec == PG_PREC_FP32) ? 4 : 8;  // FP32: one 32-bit word per cell; FP64: a double
+    const size_t elem = (p->prec == PG_PREC_FP32) ? 4 : 12;  // 32-bit words per cell: FP32 one, FP64 three
     // block tiles: rows of (nf^(d-2) x ncol) cells, the last axis padded with unfolded columns
     const int cpad = pgb::tile_col_pad(p->w), ncol = p->nf + 2 * cpad;
     const size_t plane = (size_t)ipow(p->nf, d - 2) * ncol;
     const bool f32 = (p->prec == PG_PREC_FP32);
     // leave room for the kernels' static shared memory (FP64: the kernel polynomial)
-    const size_t max_smem = prop.sharedMemPerBlockOptin - 1024 - (f32 ? 0 : sizeof(double) * pgb::kPolyCoefF64);
-    const int max_threads = f32 ? pgb::kMaxThreadsF32 : pgb::kMaxThreadsF64;
+    // (and 16 bytes for rounding the tile up to 16 bytes)
+    const size_t max_smem = prop.sharedMemPerBlockOptin - 1024 - 16 - (f32 ? 0 : sizeof(double) * pgb::kPolyCoefF64);
+    const int max_threads = f32 ? pgb::kMaxThreadsF32 : pgb::max_threads_f64(d);
     int rows_fit = (int)std::min<size_t>(p->nf, max_smem / (plane * elem));
     size_t qbytes = 0;
     if (rows_fit < p->nf) {
@@ -133,7 +134,7 @@ int build_plan(pg_boltz_plan_t *p, const pg_boltz_opts_t &o)
     p->nslab = (p->nf + rows_fit - 1) / rows_fit;
     p->rows_per_slab = (p->nf + p->nslab - 1) / p->nslab;
     p->nslab = (p->nf + p->rows_per_slab - 1) / p->rows_per_slab;  // no empty trailing slab
-    p->spread_smem = (size_t)p->rows_per_slab * plane * elem + (p->nslab > 1 ? qbytes : 0);
+    p->spread_smem = pgb::tile_bytes((size_t)p->rows_per_slab * plane, f32) + (p->nslab > 1 ? qbytes : 0);
     int per_sm = (int)(prop.sharedMemPerMultiprocessor / (p->spread_smem + 1024 + prop.reservedSharedMemPerBlock));
     per_sm = std::max(per_sm, 1);
     if (o.spread_threads > 0) {

@@ -25,9 +25,15 @@
 //  - the global folded grid holds int64 values in units of 2^-Eg, where B >= sum_p |q_p|
 //    (an upper bound written by the loss kernel) and B 2^Eg <= 2^61: no cell can overflow,
 //    and block partial sums add exactly and in any order;
-//  - FP64 kernel: each block adds into a private FP64 copy of its slab of the grid in shared
-//    memory; at the end each cell's partial sum is rounded to the grid unit (relative error
-//    2^-61 B) and added to the global grid.
+//  - FP64 kernel: each block adds into a private copy of its slab of the grid in shared memory
+//    that holds each cell as a 96-bit integer, 32 bits finer than the grid unit, in three 32-bit
+//    words (WideTile: native 32-bit atomics, the next word's only when a carry or a high part
+//    needs it).  The kernel weights are FP64; per point, a row factor R = round(q psi_a 2^(Eg+s))
+//    with a per-point scale s that keeps R below 2^62 (3D: then round(R psi_b) in integers) is
+//    formed once per row, and each contribution is round(R psi_c) from a 61-bit fixed-point psi_c
+//    by four 32 x 32-bit integer products, so no FP64 operation runs per cell (the FP64 pipe of
+//    this GPU runs at about 1/70 of the FP32 rate) and each contribution keeps about 2^-61 of its
+//    size plus 2^-32 grid units.  At the end each cell rounds to the grid unit once per block.
 //  - FP32 kernel: the private copy holds one signed 32-bit word per cell in units of 2^-Et,
 //    Et = Eg - tile_bits(d), plus per-cell carry counters in a per-block global array (SplitTile):
 //    the cell's value is word + 2^32 carry.  A contribution goes to its word with one native 32-bit
@@ -42,8 +48,8 @@
 //    to the tile unit (at most about one unit); all later additions are exact.
 //
 // Negligible pairs: a pair whose strength bound keeps every one of its points below 0.1 tile unit
-// adds exactly zero (every contribution rounds to zero), so the FP32 kernels skip it; FP64
-// kernels skip pairs whose summed bounds stay below 2^-64 B.  Each lane searches ahead for its
+// (FP64: 0.49 grid unit) adds exactly zero (every contribution rounds to zero), so the kernels
+// skip it, and points below that bound are skipped one by one.  Each lane searches ahead for its
 // next pair that is not negligible, so that the lanes of a warp spread real pairs together (with
 // the node sets of the workloads here, 25-75% of all pairs lie in the tails of f and are skipped).
 #pragma once
@@ -436,14 +442,76 @@ struct SplitTile {
     // the cell's sum in tile units
     __device__ __forceinline__ long long value(int c) const { return (long long)carry[c] * 4294967296LL + lo[c]; }
 };
-struct DoubleTile {  // FP64 path: FP64 partial sums
-    double *v;
-    // v[c] += a b (the library's shared-memory FP64 atomic add; a hand-written compare-and-swap
-    // loop around one fused multiply-add measured 2-8x slower).  No test for a zero product: the
-    // polynomial kernel weights are not zero at the support's ends as the exact kernel's are,
-    // and a zero-strength point is skipped whole (spread_point_f64).
-    __device__ __forceinline__ void add_product(int c, double a, double b) const { atomicAdd(v + c, a * b); }
+// FP64 path: one 96-bit two's-complement fixed-point value per cell in units 2^-(Eg+32), 32 bits
+// finer than the global grid (B 2^Eg < 2^61), held as a fraction word, a low and a high 32-bit
+// word in shared memory.  A contribution I + F 2^-32 (I an int64 in grid units, 0 <= F < 2^32)
+// adds F to the fraction word and I plus the carry out of that addition to the low word, each with
+// one native 32-bit atomic whose returned old value shows its carry; the high part of I plus the
+// low word's carry goes to the high word by a third atomic when not zero (for positive
+// contributions below 2^32 grid units, only on a carry).  The sum is exact in any order, and a
+// partial sum stays below 2^63 grid units.  Shared-memory FP64 atomic adds, the other choice, run
+// several times slower on this hardware (they spend the FP64 pipe).
+struct WideTile {
+    unsigned *fr;  // fraction words (shared memory)
+    unsigned *lo;  // low words
+    int *hi;       // high words
+    __device__ __forceinline__ void add(int c, long long I, unsigned F) const
+    {
+        const unsigned of = atomicAdd(fr + c, F);
+        const long long J = I + ((of + F < of) ? 1 : 0);
+        const unsigned jl = (unsigned)(unsigned long long)J;
+        const unsigned o = atomicAdd(lo + c, jl);
+        const int vh = (int)(J >> 32) + ((o + jl < o) ? 1 : 0);
+        if (vh) atomicAdd(hi + c, vh);
+    }
+    // the cell's sum rounded to the grid unit
+    __device__ __forceinline__ long long value(int c) const
+    {
+        const long long i = (long long)(((unsigned long long)(unsigned)hi[c] << 32) | lo[c]);
+        return i + (fr[c] >= 0x80000000u ? 1 : 0);
+    }
 };
+
+// Fixed-point kernel weight for the FP64 path: round(w 2^61) = h 2^31 + l with 0 <= l < 2^31
+// (w <= 1 up to the polynomial's rounding, so |h| <= 2^30 + 1).
+struct FixW {
+    int h, l;
+};
+__device__ __forceinline__ FixW fix_weight(double w)
+{
+    const long long t = __double2ll_rn(w * 2305843009213693952.0);  // 2^61
+    return FixW{(int)(t >> 31), (int)(t & 0x7fffffffll)};
+}
+
+// round(R w) for |R| < 2^62 and a fixed-point weight w: with R = Rh 2^31 + Rl (0 <= Rl < 2^31),
+// R w 2^61 = 2^62 Rh h + 2^31 (Rh l + Rl h) + Rl l, from four 32 x 32-bit integer products; the
+// last one enters truncated to 2^-30 units (error below 2^-30), the result rounds half up.
+// Every intermediate stays below 2^63 in magnitude.
+__device__ __forceinline__ long long fix_mul(long long R, FixW w)
+{
+    const int Rh = (int)(R >> 31);
+    const int Rl = (int)(R & 0x7fffffffll);
+    const long long X = (long long)Rh * w.l + (long long)Rl * w.h + (((long long)Rl * w.l) >> 31);
+    return 2 * ((long long)Rh * w.h) + ((X + (1ll << 29)) >> 30);
+}
+
+// A point's contributions in the FP64 path: each tap value v (units 2^-(Eg+s) for the point's
+// scale s) becomes I + F 2^-32 grid units with I = floor(v 2^-s), F the next 32 bits (truncated,
+// below 2^-32 grid units).
+struct TapShift {
+    int sI;    // min(s, 63): |v| < 2^62, so v >> 63 is the sign
+    int sF;    // |s - 32|
+    bool up;   // s < 32: F = v << (32 - s); otherwise F = v >> (s - 32)
+};
+__device__ __forceinline__ TapShift tap_shift(int s)
+{
+    return TapShift{min(s, 63), s < 32 ? 32 - s : s - 32, s < 32};
+}
+__device__ __forceinline__ void tap_split(long long v, const TapShift &t, long long &I, unsigned &F)
+{
+    I = v >> t.sI;
+    F = (unsigned)(unsigned long long)(t.up ? (v << t.sF) : (v >> t.sF));
+}
 
 // One post-collision point: FP32 points carry each grid coordinate (one grid cell = 1,
 // x = z n / (2 pi)) as an integer cell X (an integer-valued float) and a fraction F in [0, 1)
@@ -635,15 +703,20 @@ __device__ __forceinline__ void spread_point_f32(const SpreadArgs &p, const Poin
 
 // ---- FP64 points
 
-// Add the w^d contributions of one FP64 point to the block tile.  SLAB: the tile holds a slab of
-// the grid's rows and rows outside it are skipped; otherwise it holds every row (row_lo = 0,
-// nrows = n/2 + 1).
+// Add the w^d contributions of one FP64 point (q in grid units 2^-Eg) to the block tile.  SLAB:
+// the tile holds a slab of the grid's rows and rows outside it are skipped; otherwise it holds
+// every row (row_lo = 0, nrows = n/2 + 1).  The kernel weights are FP64.  The point works in units
+// 2^-(Eg+s) with s = 60 - ilogb|q| (at most 94), so that |q| 2^s < 2^61: each row takes the
+// integer R = round(q psi_a 2^s) (3D: then round(R psi_b) in integers) and each cell
+// round(R psi_c) from a 61-bit fixed-point psi_c (fix_mul) -- one FP64 product and conversion
+// per row instead of per cell, and about 2^-61 relative rounding -- which goes to the tile as
+// grid units and 32 fraction bits (tap_split).
 template <int D, int W, bool SLAB>
 __device__ __forceinline__ void spread_point_f64(const SpreadArgs &p, const Point<double, D> &pt,
-                                                 const DoubleTile &tile, int row_lo, int nrows, int plane)
+                                                 const WideTile &tile, int row_lo, int nrows, int plane)
 {
     const double q = pt.q;
-    if (q == 0.0) return;  // FP64 tiles add every product
+    if (q == 0.0) return;
     double w0[W];
     int r0[W];
     axis_weights_f64<W>(p, pt.x[0], w0, r0);
@@ -654,34 +727,56 @@ __device__ __forceinline__ void spread_point_f64(const SpreadArgs &p, const Poin
             r0[a] -= row_lo;
             hit |= ((unsigned)r0[a] < (unsigned)nrows);
         }
-        w0[a] *= q;
     }
     if (!hit) return;
+    const int s = max(0, min(60 - ilogb(q), 94));
+    const double qs = ldexp(q, s);
+    const TapShift ts = tap_shift(s);
     double wl[W];  // last axis: consecutive padded columns cb..cb+w-1 (clamped: x lies in [0, n/2])
     const int cb = min(max(kernel_weights_f64<W>(pt.x[D - 1], wl) + p.cpad, 0), p.ncol - W);
-    if (D == 2) {
+    FixW fl[W];
 #pragma unroll
+    for (int c = 0; c < W; ++c) fl[c] = fix_weight(wl[c]);
+    if constexpr (D == 2) {
+#pragma unroll 1
         for (int a = 0; a < W; ++a) {
             if (SLAB && (unsigned)r0[a] >= (unsigned)nrows) continue;
+            const long long R = __double2ll_rn(qs * w0[a]);
             const int row = r0[a] * plane + cb;
 #pragma unroll
-            for (int c = 0; c < W; ++c) tile.add_product(row + c, w0[a], wl[c]);
+            for (int c = 0; c < W; ++c) {
+                long long I;
+                unsigned F;
+                tap_split(fix_mul(R, fl[c]), ts, I, F);
+                tile.add(row + c, I, F);
+            }
         }
     } else {
         double w1[W];
         int c1[W];
         axis_weights_f64<W>(p, pt.x[1], w1, c1);
+        FixW f1[W];
 #pragma unroll
-        for (int b = 0; b < W; ++b) c1[b] = c1[b] * p.ncol + cb;
+        for (int b = 0; b < W; ++b) {
+            f1[b] = fix_weight(w1[b]);
+            c1[b] = c1[b] * p.ncol + cb;
+        }
+#pragma unroll 1
         for (int a = 0; a < W; ++a) {
             if (SLAB && (unsigned)r0[a] >= (unsigned)nrows) continue;
+            const long long Ra = __double2ll_rn(qs * w0[a]);
             const int row = r0[a] * plane;
-#pragma unroll
+#pragma unroll 1
             for (int b = 0; b < W; ++b) {
-                const double wab = w0[a] * w1[b];
+                const long long R = fix_mul(Ra, f1[b]);
                 const int line = row + c1[b];
 #pragma unroll
-                for (int c = 0; c < W; ++c) tile.add_product(line + c, wab, wl[c]);
+                for (int c = 0; c < W; ++c) {
+                    long long I;
+                    unsigned F;
+                    tap_split(fix_mul(R, fl[c]), ts, I, F);
+                    tile.add(line + c, I, F);
+                }
             }
         }
     }
@@ -847,8 +942,8 @@ __device__ __forceinline__ void queue_spread(const SpreadArgs &p, const T *buf, 
 
 // The pairs pr = first, first + nthr, ... below end of one thread, spread through the warp's
 // queue `buf` (spread_queue_values(d, fp32) x 32 values) into one slab (SLAB) or a tile that
-// holds every row; without slabs the queue only leaves out the FP32 points that add exactly zero,
-// so that every lane spreads a real point.  Every loop condition is uniform over the warp.
+// holds every row.  Points below floor_q (they add exactly zero) are not queued, so that every
+// lane spreads a real point.  Every loop condition is uniform over the warp.
 template <typename T, int D, int W, typename Tile, bool ANG, bool SLAB = true>
 __device__ __forceinline__ void spread_pairs_queued(const SpreadArgs &p, long long first, long long end,
                                                     long long nthr, T sc, T tau, T floor_q, const Tile &tile,
@@ -869,8 +964,8 @@ __device__ __forceinline__ void spread_pairs_queued(const SpreadArgs &p, long lo
             bool hit = false;
             if (ok) {
                 make_point<T, D, ANG>(p, P, qbase, m, pt);
-                // FP32 points below kNegligibleF32 add exactly zero and are not queued
-                hit = sizeof(T) == 8 || fabs(pt.q) >= T(kNegligibleF32);
+                // points below floor_q add exactly zero and are not queued
+                hit = fabs(pt.q) >= floor_q;
                 if constexpr (SLAB) hit = hit && rows_hit<T, D, W>(p, pt, row_lo, nrows);
             }
             const unsigned mask = __ballot_sync(full, hit);
@@ -948,12 +1043,12 @@ __global__ void __launch_bounds__(kMaxThreadsF32) k_spread_f32(const __grid_cons
     long long first, nthr;
     pair_schedule(p, first, nthr);
     if (p.nslab > 1) {
-        float *buf = reinterpret_cast<float *>(smem_raw + (size_t)p.rows_per_slab * G.plane * 4) +
+        float *buf = reinterpret_cast<float *>(smem_raw + tile_bytes((size_t)p.rows_per_slab * G.plane, true)) +
                      (threadIdx.x >> 5) * 32 * spread_queue_values(D, true);
         spread_pairs_queued<float, D, W, SplitTile, ANG>(p, first, p.npairs, nthr, sc, tau, kNegligibleF32, tile,
                                                           G.row_lo, G.nrows, G.plane, buf);
     } else if (p.queued) {  // one slab: the queues only compact the points that add something
-        float *buf = reinterpret_cast<float *>(smem_raw + (size_t)G.ncell * 4) +
+        float *buf = reinterpret_cast<float *>(smem_raw + tile_bytes(G.ncell, true)) +
                      (threadIdx.x >> 5) * 32 * spread_queue_values(D, true);
         spread_pairs_queued<float, D, W, SplitTile, ANG, false>(p, first, p.npairs, nthr, sc, tau, kNegligibleF32,
                                                                  tile, 0, G.nrows, G.plane, buf);
@@ -972,40 +1067,44 @@ __global__ void __launch_bounds__(kMaxThreadsF32) k_spread_f32(const __grid_cons
 }
 
 template <int D, int W, bool ANG>
-__global__ void __launch_bounds__(kMaxThreadsF64) k_spread_f64(const __grid_constant__ SpreadArgs p)
+__global__ void __launch_bounds__(max_threads_f64(D), 1) k_spread_f64(const __grid_constant__ SpreadArgs p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SlabGeom G = slab_geometry(p, D);
     if (G.nrows <= 0) return;  // uniform over the block
-    DoubleTile tile{reinterpret_cast<double *>(smem_raw)};
-    for (int c = threadIdx.x; c < G.ncell; c += blockDim.x) tile.v[c] = 0.0;
+    // fraction, low and high words of rows_per_slab x plane cells each
+    const size_t tile_cells = (size_t)p.rows_per_slab * G.plane;
+    unsigned *words = reinterpret_cast<unsigned *>(smem_raw);
+    const WideTile tile{words, words + tile_cells, reinterpret_cast<int *>(words + 2 * tile_cells)};
+    for (int c = threadIdx.x; c < G.ncell; c += blockDim.x) {
+        tile.fr[c] = 0u;
+        tile.lo[c] = 0u;
+        tile.hi[c] = 0;
+    }
     load_kernel_poly(p.kpoly);
     __syncthreads();
     const double Bnd = *p.bound;
     const int Eg = global_exponent(Bnd);
     const double tau = *p.tau;
+    const double sc = ldexp(1.0, Eg);  // strengths in grid units
     // pairs whose summed strength bounds stay below 2^-64 B are skipped (per-point bound below
-    // floor_q, and at most npairs pairs)
-    const double floor_q = ldexp(Bnd, -64) * p.cd.wmax / (double)p.npairs;
+    // floor_q, and at most npairs pairs): 2^-3 grid units at most in all
+    const double floor_q = ldexp(Bnd, Eg - 64) * p.cd.wmax / (double)p.npairs;
     long long first, nthr;
     pair_schedule(p, first, nthr);
     if (p.nslab > 1) {
-        double *buf = reinterpret_cast<double *>(smem_raw + (size_t)p.rows_per_slab * G.plane * 8) +
+        double *buf = reinterpret_cast<double *>(smem_raw + tile_bytes(tile_cells, false)) +
                       (threadIdx.x >> 5) * 32 * spread_queue_values(D, false);
-        spread_pairs_queued<double, D, W, DoubleTile, ANG>(p, first, p.npairs, nthr, 1.0, tau, floor_q, tile,
-                                                            G.row_lo, G.nrows, G.plane, buf);
+        spread_pairs_queued<double, D, W, WideTile, ANG>(p, first, p.npairs, nthr, sc, tau, floor_q, tile, G.row_lo,
+                                                          G.nrows, G.plane, buf);
     } else {
-        spread_pairs<double, D, W, DoubleTile, ANG>(p, first, p.npairs, nthr, 1.0, tau, floor_q, tile, G.row_lo,
-                                                     G.nrows, G.plane);
+        spread_pairs<double, D, W, WideTile, ANG>(p, first, p.npairs, nthr, sc, tau, floor_q, tile, G.row_lo,
+                                                   G.nrows, G.plane);
     }
     __syncthreads();
-    // block partial sums -> the grid's fixed-point unit (|v| 2^Eg <= 2^61); the rounding of a
-    // partial sum is 2^-61 B at most
-    const double sc = ldexp(1.0, Eg);
     for (int c = threadIdx.x; c < G.ncell; c += blockDim.x) {
-        const long long v = __double2ll_rn(tile.v[c] * sc);
-        if (v)
-            atomicAdd(p.grid + tile_to_grid_cell(c, D, p.nf, p.ncol, p.cpad, p.n, G.row_lo), (unsigned long long)v);
+        const long long v = tile.value(c);
+        if (v) atomicAdd(p.grid + tile_to_grid_cell(c, D, p.nf, p.ncol, p.cpad, p.n, G.row_lo), (unsigned long long)v);
     }
 }
 
