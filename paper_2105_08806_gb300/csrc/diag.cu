@@ -73,8 +73,9 @@ __global__ void k_grid_coords(const float *v, long long n, pgb::TypedConsts<floa
                               double *frac, double *m2)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        float X, F, w;
-        pgb::spread_detail::grid_coord_f32(K, v[i], alg != 0, X, F, w);
+        float X, F;
+        pgb::spread_detail::grid_coord_f32(K, v[i], alg != 0, X, F);
+        const float w = pgb::spread_detail::axis_m2_f32(K, v[i], alg != 0);
         cell[i] = (double)X;
         frac[i] = (double)F;
         m2[i] = (double)w;

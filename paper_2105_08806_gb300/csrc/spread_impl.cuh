@@ -199,26 +199,32 @@ __device__ __forceinline__ float atan_correction_f32(float u)
     return u * s * r;
 }
 
+// The factor mu^-2 of one mapped coordinate v in a point's strength (Section 2.1), FP32:
+// (S^2 + v^2)/S (algebraic map) or S cosh(v/S) = S (e^-|v/S| + e^|v/S|)/2 (logarithmic map).
+__device__ __forceinline__ float axis_m2_f32(const TypedConsts<float> &K, float v, bool alg)
+{
+    if (alg) return fmaf(v, v, K.SS) * K.invS;
+    const float w = fmaf(v, K.invS, v * K.invS_lo);
+    const float e = exp2f(-fabsf(w) * 1.4426950408889634f);
+    return 0.5f * K.S * (__frcp_rn(e) + e);
+}
+
 // FP32 grid coordinate x = z n/(2 pi) of the angle z = arccos(xi(v)) of one mapped coordinate, as an
-// integer cell X (an integer-valued float) and a fraction F in [0, 1), and the weight
-// mu(xi(v))^-2 (Section 2.1).  With w = v/S:
+// integer cell X (an integer-valued float) and a fraction F in [0, 1) (Section 2.1).  With w = v/S:
 //   r = 1: |w| <= 1: x = n/4 - gs atan(w);  w > 1: x = gs atan(S/v);  w < -1: x = n/2 + gs atan(S/v)
-//          (z = pi/2 - atan(w) = atan(1/w) or pi + atan(1/w)),          mu^-2 = (S^2 + v^2)/S
-//   r = 0: x = 2 gs atan(e) (v >= 0) or n/2 - 2 gs atan(e) (v < 0), e = exp(-|v|/S),
-//          mu^-2 = S (1/e + e)/2
+//          (z = pi/2 - atan(w) = atan(1/w) or pi + atan(1/w))
+//   r = 0: x = 2 gs atan(e) (v >= 0) or n/2 - 2 gs atan(e) (v < 0), e = exp(-|v|/S)
 // with gs = n/(2 pi), i.e. x = base - sg c atan(u) with |u| <= 1 and base in {0, n/4, n/2}.  The
 // offsets are exact, c = gs (or 2 gs) is a two-term constant, atan(u) = u + correction is
 // renormalised into two terms (Fast2Sum) and multiplied by c with its exact FMA residual, and
 // base - sg c atan(u) is summed exactly (Fast2Sum), so the fraction F is accurate to about 1e-7
 // of a cell: a grid coordinate rounded to FP32 as a whole (about 1e-6 of a cell at x ~ 100)
 // shifts points that share a coordinate -- and many do, on a tensor grid of nodes -- coherently.
-__device__ __forceinline__ void grid_coord_f32(const TypedConsts<float> &K, float v, bool alg, float &X, float &F,
-                                               float &m2)
+__device__ __forceinline__ void grid_coord_f32(const TypedConsts<float> &K, float v, bool alg, float &X, float &F)
 {
     float base, sg, u, ch = K.gs, cl = K.gs_lo;
     if (alg) {
         const float w = fmaf(v, K.invS, v * K.invS_lo);  // v/S
-        m2 = fmaf(v, v, K.SS) * K.invS;
         if (fabsf(w) <= 1.0f) {
             base = K.xq;
             sg = 1.0f;
@@ -233,7 +239,6 @@ __device__ __forceinline__ void grid_coord_f32(const TypedConsts<float> &K, floa
     } else {
         const float w = fmaf(v, K.invS, v * K.invS_lo);
         const float e = exp2f(-fabsf(w) * 1.4426950408889634f);  // exp(-|v|/S)
-        m2 = 0.5f * K.S * (__frcp_rn(e) + e);
         u = e;
         base = v >= 0.0f ? 0.0f : 2.0f * K.xq;
         sg = v >= 0.0f ? -1.0f : 1.0f;
@@ -527,17 +532,16 @@ struct Point<double, D> {
     double x[D], q;
 };
 
-// Point m of pair P (qbase = a_i a_j B x multiplicity x tile scale).
-template <typename T, int D, bool ANG = false>
-__device__ __forceinline__ void make_point(const SpreadArgs &p, const PairData<T, D> &P, T qbase, int m,
-                                           Point<T, D> &pt)
+// Strength of point m of pair P before the map factors: qbase w_m, times the even part of
+// b(cos theta) for angular kernels (Horner in cos^2 theta).
+template <typename T, int D, bool ANG>
+__device__ __forceinline__ T point_base(const SpreadArgs &p, const PairData<T, D> &P, T qbase, int m)
 {
     const T *sig = static_cast<const T *>(p.sig);
     const T *wsig = static_cast<const T *>(p.wsig);
-    const TypedConsts<T> &K = kconst<T>(p);
-    const bool alg = (p.r == 1);
     T q = qbase * wsig[m];
-    if constexpr (ANG) {  // even part of b(cos theta), Horner in cos^2 theta
+    if constexpr (ANG) {
+        const TypedConsts<T> &K = kconst<T>(p);
         T c = T(0);
 #pragma unroll
         for (int l = 0; l < D; ++l) c += P.dir[l] * sig[m * D + l];
@@ -546,14 +550,47 @@ __device__ __forceinline__ void make_point(const SpreadArgs &p, const PairData<T
         for (int k = p.nang_even - 2; k >= 0; --k) be = be * c2 + K.ang_even[k];
         q *= be;
     }
+    return q;
+}
+
+// FP32: the post-collision velocity v' = (v_i + v_j)/2 + |v_i - v_j| sigma_m / 2 of point m of
+// pair P and its strength q (qbase = a_i a_j B x multiplicity x tile scale), without the grid
+// coordinates.
+template <int D, bool ANG>
+__device__ __forceinline__ float point_velocity_f32(const SpreadArgs &p, const PairData<float, D> &P, float qbase,
+                                                    int m, float (&vp)[D])
+{
+    const float *sig = static_cast<const float *>(p.sig);
+    const TypedConsts<float> &K = kconst<float>(p);
+    const bool alg = (p.r == 1);
+    float q = point_base<float, D, ANG>(p, P, qbase, m);
 #pragma unroll
     for (int l = 0; l < D; ++l) {
-        const T vp = P.cen[l] + P.rad * sig[m * D + l];
-        T m2;
-        if constexpr (sizeof(T) == 4) {
-            grid_coord_f32(K, vp, alg, pt.X[l], pt.F[l], m2);
-        } else {
-            double z;
+        vp[l] = fmaf(P.rad, sig[m * D + l], P.cen[l]);
+        q *= axis_m2_f32(K, vp[l], alg);
+    }
+    return q;
+}
+
+// Point m of pair P (qbase = a_i a_j B x multiplicity x tile scale).
+template <typename T, int D, bool ANG = false>
+__device__ __forceinline__ void make_point(const SpreadArgs &p, const PairData<T, D> &P, T qbase, int m,
+                                           Point<T, D> &pt)
+{
+    const TypedConsts<T> &K = kconst<T>(p);
+    const bool alg = (p.r == 1);
+    if constexpr (sizeof(T) == 4) {
+        float vp[D];
+        pt.q = point_velocity_f32<D, ANG>(p, P, qbase, m, vp);
+#pragma unroll
+        for (int l = 0; l < D; ++l) grid_coord_f32(K, vp[l], alg, pt.X[l], pt.F[l]);
+    } else {
+        const double *sig = static_cast<const double *>(p.sig);
+        double q = point_base<double, D, ANG>(p, P, qbase, m);
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+            const double vp = P.cen[l] + P.rad * sig[m * D + l];
+            double z, m2;
             if (alg) {
                 z = Fn<T>::atan2_(K.S, vp);
                 m2 = (K.SS + vp * vp) * K.invS;
@@ -567,10 +604,10 @@ __device__ __forceinline__ void make_point(const SpreadArgs &p, const PairData<T
                 m2 = 0.5 * K.S * (e + 1.0 / e);
             }
             pt.x[l] = z * K.gs;
+            q *= m2;
         }
-        q *= m2;
+        pt.q = q;
     }
-    pt.q = q;
 }
 
 // Tile layout.  A block tile holds rows row_lo..row_lo+nrows-1 of axis 0 of the folded grid, and
@@ -898,57 +935,104 @@ __device__ __forceinline__ bool rows_hit(const SpreadArgs &p, const Point<T, D> 
     return hit;
 }
 
-// Queue slot layout per warp: FP32 points X[D], F[D], q; FP64 points x[D], q (32 slots each).
-template <typename T, int D>
-__device__ __forceinline__ void queue_put(T *buf, int slot, const Point<T, D> &pt)
-{
+// What a warp queue holds for one point.  LATE (FP32 without slabs): the post-collision velocity
+// v'[D] and the strength q, so that the grid coordinates are formed after the queue and only for
+// the points that add something; otherwise the point itself (FP32: X[D], F[D], q; FP64: x[D], q).
+// Slot layout: value k of slot j at buf[32 k + j].
+template <typename T, int D, bool LATE>
+struct QEntry {
+    Point<T, D> pt;
+    __device__ __forceinline__ T q() const { return pt.q; }
+    __device__ __forceinline__ void put(T *buf, int slot) const
+    {
 #pragma unroll
-    for (int l = 0; l < D; ++l) {
-        if constexpr (sizeof(T) == 4) {
-            buf[l * 32 + slot] = pt.X[l];
-            buf[(D + l) * 32 + slot] = pt.F[l];
-        } else {
-            buf[l * 32 + slot] = pt.x[l];
+        for (int l = 0; l < D; ++l) {
+            if constexpr (sizeof(T) == 4) {
+                buf[l * 32 + slot] = pt.X[l];
+                buf[(D + l) * 32 + slot] = pt.F[l];
+            } else {
+                buf[l * 32 + slot] = pt.x[l];
+            }
         }
+        buf[(sizeof(T) == 4 ? 2 * D : D) * 32 + slot] = pt.q;
     }
-    buf[(sizeof(T) == 4 ? 2 * D : D) * 32 + slot] = pt.q;
-}
-
-template <typename T, int D>
-__device__ __forceinline__ void queue_get(const T *buf, int slot, Point<T, D> &pt)
-{
+    __device__ __forceinline__ void get(const T *buf, int slot)
+    {
 #pragma unroll
-    for (int l = 0; l < D; ++l) {
-        if constexpr (sizeof(T) == 4) {
-            pt.X[l] = buf[l * 32 + slot];
-            pt.F[l] = buf[(D + l) * 32 + slot];
-        } else {
-            pt.x[l] = buf[l * 32 + slot];
+        for (int l = 0; l < D; ++l) {
+            if constexpr (sizeof(T) == 4) {
+                pt.X[l] = buf[l * 32 + slot];
+                pt.F[l] = buf[(D + l) * 32 + slot];
+            } else {
+                pt.x[l] = buf[l * 32 + slot];
+            }
         }
+        pt.q = buf[(sizeof(T) == 4 ? 2 * D : D) * 32 + slot];
     }
-    pt.q = buf[(sizeof(T) == 4 ? 2 * D : D) * 32 + slot];
-}
+    template <bool ANG>
+    __device__ __forceinline__ void make(const SpreadArgs &p, const PairData<T, D> &P, T qbase, int m)
+    {
+        make_point<T, D, ANG>(p, P, qbase, m, pt);
+    }
+    __device__ __forceinline__ void point(const SpreadArgs &, Point<T, D> &out) const { out = pt; }
+};
+template <int D>
+struct QEntry<float, D, true> {
+    float v[D], qv;
+    __device__ __forceinline__ float q() const { return qv; }
+    __device__ __forceinline__ void put(float *buf, int slot) const
+    {
+#pragma unroll
+        for (int l = 0; l < D; ++l) buf[l * 32 + slot] = v[l];
+        buf[D * 32 + slot] = qv;
+    }
+    __device__ __forceinline__ void get(const float *buf, int slot)
+    {
+#pragma unroll
+        for (int l = 0; l < D; ++l) v[l] = buf[l * 32 + slot];
+        qv = buf[D * 32 + slot];
+    }
+    template <bool ANG>
+    __device__ __forceinline__ void make(const SpreadArgs &p, const PairData<float, D> &P, float qbase, int m)
+    {
+        qv = point_velocity_f32<D, ANG>(p, P, qbase, m, v);
+    }
+    // the same point make_point forms (same velocity, strength and coordinates)
+    __device__ __forceinline__ void point(const SpreadArgs &p, Point<float, D> &out) const
+    {
+        const TypedConsts<float> &K = kconst<float>(p);
+        const bool alg = (p.r == 1);
+#pragma unroll
+        for (int l = 0; l < D; ++l) grid_coord_f32(K, v[l], alg, out.X[l], out.F[l]);
+        out.q = qv;
+    }
+};
 
 // Spread queue slot `lane` (when valid) with the whole warp.
-template <typename T, int D, int W, typename Tile, bool SLAB>
+template <typename T, int D, int W, typename Tile, bool SLAB, bool LATE>
 __device__ __forceinline__ void queue_spread(const SpreadArgs &p, const T *buf, int lane, bool valid,
                                              const Tile &tile, int row_lo, int nrows, int plane)
 {
     if (!valid) return;
+    QEntry<T, D, LATE> e;
+    e.get(buf, lane);
     Point<T, D> pt;
-    queue_get<T, D>(buf, lane, pt);
+    e.point(p, pt);
     spread_point_any<T, D, W, Tile, SLAB>(p, pt, tile, row_lo, nrows, plane);
 }
 
 // The pairs pr = first, first + nthr, ... below end of one thread, spread through the warp's
 // queue `buf` (spread_queue_values(d, fp32) x 32 values) into one slab (SLAB) or a tile that
 // holds every row.  Points below floor_q (they add exactly zero) are not queued, so that every
-// lane spreads a real point.  Every loop condition is uniform over the warp.
+// lane spreads a real point; FP32 points without slabs queue their velocity and strength and
+// form their grid coordinates after the queue (QEntry).  Every loop condition is uniform over
+// the warp.
 template <typename T, int D, int W, typename Tile, bool ANG, bool SLAB = true>
 __device__ __forceinline__ void spread_pairs_queued(const SpreadArgs &p, long long first, long long end,
                                                     long long nthr, T sc, T tau, T floor_q, const Tile &tile,
                                                     int row_lo, int nrows, int plane, T *buf)
 {
+    constexpr bool LATE = (sizeof(T) == 4) && !SLAB;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -960,22 +1044,22 @@ __device__ __forceinline__ void spread_pairs_queued(const SpreadArgs &p, long lo
         if (!__any_sync(full, ok)) break;
         const T qbase = ok ? P.base * sc : T(0);
         for (int m = 0; m < p.M; ++m) {
-            Point<T, D> pt;
+            QEntry<T, D, LATE> e;
             bool hit = false;
             if (ok) {
-                make_point<T, D, ANG>(p, P, qbase, m, pt);
+                e.template make<ANG>(p, P, qbase, m);
                 // points below floor_q add exactly zero and are not queued
-                hit = fabs(pt.q) >= floor_q;
-                if constexpr (SLAB) hit = hit && rows_hit<T, D, W>(p, pt, row_lo, nrows);
+                hit = fabs(e.q()) >= floor_q;
+                if constexpr (SLAB) hit = hit && rows_hit<T, D, W>(p, e.pt, row_lo, nrows);
             }
             const unsigned mask = __ballot_sync(full, hit);
             const int n = __popc(mask), rank = __popc(mask & lt), room = 32 - count;
-            if (hit && rank < room) queue_put<T, D>(buf, count + rank, pt);
+            if (hit && rank < room) e.put(buf, count + rank);
             if (n >= room) {  // full: spread 32 points, then queue the rest
                 __syncwarp();
-                queue_spread<T, D, W, Tile, SLAB>(p, buf, lane, true, tile, row_lo, nrows, plane);
+                queue_spread<T, D, W, Tile, SLAB, LATE>(p, buf, lane, true, tile, row_lo, nrows, plane);
                 __syncwarp();
-                if (hit && rank >= room) queue_put<T, D>(buf, rank - room, pt);
+                if (hit && rank >= room) e.put(buf, rank - room);
                 count = n - room;
             } else {
                 count += n;
@@ -984,7 +1068,7 @@ __device__ __forceinline__ void spread_pairs_queued(const SpreadArgs &p, long lo
         if (ok) pr += nthr;
     }
     __syncwarp();
-    queue_spread<T, D, W, Tile, SLAB>(p, buf, lane, lane < count, tile, row_lo, nrows, plane);
+    queue_spread<T, D, W, Tile, SLAB, LATE>(p, buf, lane, lane < count, tile, row_lo, nrows, plane);
 }
 
 struct SlabGeom {
