@@ -364,7 +364,7 @@ def measure_config(name, args, dev, stream, timer, peaks, world):
         row["norm_Q_over_norm_gain"] = float(np.linalg.norm(q64)) / mom64["norm_gain"]
         row["speedup_fp32_vs_fp64"] = mean64 / mean32
     else:
-        row["fp64"] = {"skipped": "not timed by default: one FP64 evaluation takes about two minutes here "
+        row["fp64"] = {"skipped": "not timed by default: one FP64 evaluation takes about 77 s here "
                                   "(--fp64-steps 1 times it)" if (d == 3 and N > 16 and args.fp64_steps < 0)
                        else "--no-fp64-3d or --fp64-steps 0"}
         row["norm_Q_over_norm_gain"] = float(np.linalg.norm(q32)) / mom32["norm_gain"]

@@ -72,10 +72,12 @@ def test_all_modes_match_oracle(case, prec):
     if prec == PG_PREC_FP64:
         assert err < TOL64, (err, info)
     else:
-        # FP32 rounding scales with the gain term; these small cases have |Q| down to 0.2 |Q+|,
-        # so the FP32 bar is taken against the gain norm here (full-size workloads use |Q|).
+        # relative L2 of Q (the gain-normalised figure beside it).  These plans take tol 1e-7: on
+        # grids of 10-60 cells the transform's own truncation at tol 1e-6 reaches several tol of
+        # the gain norm (R7), and |Q| is 0.09-0.35 of |Q+| here (measured 2.7e-5 of |Q| at N = 2)
         err_gain = float(np.linalg.norm(Q - Qref) / np.linalg.norm(gain))
-        assert err_gain < TOL32, (err, err_gain, info)
+        print(f"FP32 {case}: {err:.2e} of |Q|, {err_gain:.2e} of |Q+|")
+        assert err < TOL32, (err, err_gain, info)
     # gain term parity through the moments' norm of Q+
     assert abs(mom["norm_gain"] - np.linalg.norm(gain)) <= (1e-10 if prec == PG_PREC_FP64 else 1e-5) * np.linalg.norm(gain)
     if r == 1 and N >= 2:
@@ -116,7 +118,7 @@ FULL_SIZE = [
     ("2d-maxwell", "c1_2d_maxwell", True),
     ("2d-hard-spheres", "c2_2d_vhs", True),
     ("3d-bkw", "c3_3d_bkw", True),
-    ("3d-bimaxwell", "c4_3d_bimaxwell", False),  # the FP64 path takes two minutes per evaluation here
+    ("3d-bimaxwell", "c4_3d_bimaxwell", False),  # the FP64 path takes 77 s per evaluation here
 ]
 
 
@@ -128,7 +130,7 @@ def test_full_size_fp32_against_oracle_and_fp64_path(name, ctor, full):
     * where the FP64 path is affordable, the relative L2 error over ALL modes against the FP64
       path -- itself within 1e-10 of the oracle on the stored modes -- is at most 1e-5 of |Q|, and
       the stored modes are within 1e-6 of the gain norm there;
-    * for the 3D gamma = 1/2 workload, whose FP64 evaluation takes two minutes, the stored modes
+    * for the 3D gamma = 1/2 workload, whose FP64 evaluation takes 77 s, the stored modes
       alone are within 1e-5 of |Q| there (these modes weigh the small high modes more than all
       modes do: on the 3D BKW workload their figure is five times the all-mode one).
     Mode-level mass and energy (Section 3.3) within 2e-6 of the gain's.  The errors against |Q|
