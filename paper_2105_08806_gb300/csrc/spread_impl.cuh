@@ -917,6 +917,17 @@ __device__ __forceinline__ void spread_pairs(const SpreadArgs &p, long long firs
 // Instead each warp appends the points that hit its slab to a queue of 32 entries in shared
 // memory (slot-major) and spreads a full queue with all 32 lanes, one point per lane.
 
+// Whether any of the w axis-0 rows of a point whose first tap is s lies in the slab.
+template <int W>
+__device__ __forceinline__ bool rows_hit_from(const SpreadArgs &p, int s, int row_lo, int nrows)
+{
+    const bool simple = p.simple_fold != 0;
+    bool hit = false;
+#pragma unroll
+    for (int a = 0; a < W; ++a) hit |= (unsigned)(fold_cell(s + a, p.n, simple) - row_lo) < (unsigned)nrows;
+    return hit;
+}
+
 // Whether any of the w axis-0 rows of a point lies in the slab (the rows of the point's spreading).
 template <typename T, int D, int W>
 __device__ __forceinline__ bool rows_hit(const SpreadArgs &p, const Point<T, D> &pt, int row_lo, int nrows)
@@ -928,18 +939,15 @@ __device__ __forceinline__ bool rows_hit(const SpreadArgs &p, const Point<T, D> 
     } else {
         s = (int)floor(pt.x[0] - 0.5 * W) + 1;
     }
-    const bool simple = p.simple_fold != 0;
-    bool hit = false;
-#pragma unroll
-    for (int a = 0; a < W; ++a) hit |= (unsigned)(fold_cell(s + a, p.n, simple) - row_lo) < (unsigned)nrows;
-    return hit;
+    return rows_hit_from<W>(p, s, row_lo, nrows);
 }
 
-// What a warp queue holds for one point.  LATE (FP32 without slabs): the post-collision velocity
-// v'[D] and the strength q, so that the grid coordinates are formed after the queue and only for
-// the points that add something; otherwise the point itself (FP32: X[D], F[D], q; FP64: x[D], q).
+// What a warp queue holds for one point.  LATE (FP32): the post-collision velocity v'[D] and the
+// strength q, so that the grid coordinates are formed after the queue and only for the points that
+// go there -- in a slabbed grid (SLAB) with the axis-0 coordinate X0 + F0 formed before, for the
+// slab test; otherwise (FP64) the point itself, x[D] and q.
 // Slot layout: value k of slot j at buf[32 k + j].
-template <typename T, int D, bool LATE>
+template <typename T, int D, bool LATE, bool SLAB>
 struct QEntry {
     Point<T, D> pt;
     __device__ __forceinline__ T q() const { return pt.q; }
@@ -974,28 +982,49 @@ struct QEntry {
     {
         make_point<T, D, ANG>(p, P, qbase, m, pt);
     }
+    template <int W>
+    __device__ __forceinline__ bool in_slab(const SpreadArgs &p, int row_lo, int nrows)
+    {
+        return rows_hit<T, D, W>(p, pt, row_lo, nrows);
+    }
     __device__ __forceinline__ void point(const SpreadArgs &, Point<T, D> &out) const { out = pt; }
 };
-template <int D>
-struct QEntry<float, D, true> {
-    float v[D], qv;
+template <int D, bool SLAB>
+struct QEntry<float, D, true, SLAB> {
+    float v[D], qv, X0, F0;
     __device__ __forceinline__ float q() const { return qv; }
     __device__ __forceinline__ void put(float *buf, int slot) const
     {
 #pragma unroll
         for (int l = 0; l < D; ++l) buf[l * 32 + slot] = v[l];
         buf[D * 32 + slot] = qv;
+        if constexpr (SLAB) {
+            buf[(D + 1) * 32 + slot] = X0;
+            buf[(D + 2) * 32 + slot] = F0;
+        }
     }
     __device__ __forceinline__ void get(const float *buf, int slot)
     {
 #pragma unroll
         for (int l = 0; l < D; ++l) v[l] = buf[l * 32 + slot];
         qv = buf[D * 32 + slot];
+        if constexpr (SLAB) {
+            X0 = buf[(D + 1) * 32 + slot];
+            F0 = buf[(D + 2) * 32 + slot];
+        }
     }
     template <bool ANG>
     __device__ __forceinline__ void make(const SpreadArgs &p, const PairData<float, D> &P, float qbase, int m)
     {
         qv = point_velocity_f32<D, ANG>(p, P, qbase, m, v);
+    }
+    // slabs: the axis-0 coordinate, then whether one of the point's rows lies in the slab
+    template <int W>
+    __device__ __forceinline__ bool in_slab(const SpreadArgs &p, int row_lo, int nrows)
+    {
+        grid_coord_f32(kconst<float>(p), v[0], p.r == 1, X0, F0);
+        float t0;
+        return rows_hit_from<W>(p, first_tap_f32<W>(X0, F0, t0), row_lo, nrows);
     }
     // the same point make_point forms (same velocity, strength and coordinates)
     __device__ __forceinline__ void point(const SpreadArgs &p, Point<float, D> &out) const
@@ -1003,7 +1032,14 @@ struct QEntry<float, D, true> {
         const TypedConsts<float> &K = kconst<float>(p);
         const bool alg = (p.r == 1);
 #pragma unroll
-        for (int l = 0; l < D; ++l) grid_coord_f32(K, v[l], alg, out.X[l], out.F[l]);
+        for (int l = 0; l < D; ++l) {
+            if (SLAB && l == 0) {
+                out.X[0] = X0;
+                out.F[0] = F0;
+            } else {
+                grid_coord_f32(K, v[l], alg, out.X[l], out.F[l]);
+            }
+        }
         out.q = qv;
     }
 };
@@ -1014,7 +1050,7 @@ __device__ __forceinline__ void queue_spread(const SpreadArgs &p, const T *buf, 
                                              const Tile &tile, int row_lo, int nrows, int plane)
 {
     if (!valid) return;
-    QEntry<T, D, LATE> e;
+    QEntry<T, D, LATE, SLAB> e;
     e.get(buf, lane);
     Point<T, D> pt;
     e.point(p, pt);
@@ -1024,15 +1060,15 @@ __device__ __forceinline__ void queue_spread(const SpreadArgs &p, const T *buf, 
 // The pairs pr = first, first + nthr, ... below end of one thread, spread through the warp's
 // queue `buf` (spread_queue_values(d, fp32) x 32 values) into one slab (SLAB) or a tile that
 // holds every row.  Points below floor_q (they add exactly zero) are not queued, so that every
-// lane spreads a real point; FP32 points without slabs queue their velocity and strength and
-// form their grid coordinates after the queue (QEntry).  Every loop condition is uniform over
-// the warp.
+// lane spreads a real point; FP32 points queue their velocity and strength and form their grid
+// coordinates after the queue (QEntry; with slabs, all but axis 0's).  Every loop condition is
+// uniform over the warp.
 template <typename T, int D, int W, typename Tile, bool ANG, bool SLAB = true>
 __device__ __forceinline__ void spread_pairs_queued(const SpreadArgs &p, long long first, long long end,
                                                     long long nthr, T sc, T tau, T floor_q, const Tile &tile,
                                                     int row_lo, int nrows, int plane, T *buf)
 {
-    constexpr bool LATE = (sizeof(T) == 4) && !SLAB;
+    constexpr bool LATE = (sizeof(T) == 4);
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -1044,13 +1080,13 @@ __device__ __forceinline__ void spread_pairs_queued(const SpreadArgs &p, long lo
         if (!__any_sync(full, ok)) break;
         const T qbase = ok ? P.base * sc : T(0);
         for (int m = 0; m < p.M; ++m) {
-            QEntry<T, D, LATE> e;
+            QEntry<T, D, LATE, SLAB> e;
             bool hit = false;
             if (ok) {
                 e.template make<ANG>(p, P, qbase, m);
                 // points below floor_q add exactly zero and are not queued
                 hit = fabs(e.q()) >= floor_q;
-                if constexpr (SLAB) hit = hit && rows_hit<T, D, W>(p, e.pt, row_lo, nrows);
+                if constexpr (SLAB) hit = hit && e.template in_slab<W>(p, row_lo, nrows);
             }
             const unsigned mask = __ballot_sync(full, hit);
             const int n = __popc(mask), rank = __popc(mask & lt), room = 32 - count;
