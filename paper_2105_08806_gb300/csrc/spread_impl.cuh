@@ -431,6 +431,24 @@ struct SplitTile {
         const int r = (int)((unsigned)o + (unsigned)v);
         if (((o ^ r) & (v ^ r)) < 0) atomicAdd(carry + c, d);
     }
+    // The same addition for a run of consecutive cells: the wrap of this addition is shifted
+    // into `mask` (one funnel shift) and the carries of the run are added afterwards, in
+    // add_carries, where the mask is rarely non-zero.
+    __device__ __forceinline__ unsigned add_int_run(int c, int v, unsigned mask) const
+    {
+        const int o = atomicAdd(lo + c, v);
+        const int r = (int)((unsigned)o + (unsigned)v);
+        return __funnelshift_l((unsigned)((o ^ r) & (v ^ r)), mask, 1);
+    }
+    // carries of a run of n additions to cells c0 .. c0+n-1 (bit n-1-k of mask: cell c0 + k)
+    __device__ __forceinline__ void add_carries(int c0, int n, unsigned mask, int d) const
+    {
+        while (mask) {
+            const int b = __ffs(mask) - 1;
+            atomicAdd(carry + c0 + (n - 1 - b), d);
+            mask &= mask - 1;
+        }
+    }
     __device__ __forceinline__ void add64(int c, long long x) const
     {
         const int xl = (int)(unsigned)(unsigned long long)x;  // low word, signed
@@ -677,8 +695,10 @@ __device__ __forceinline__ void spread_point_f32(const SpreadArgs &p, const Poin
                 }
                 const int rq = __float2int_rn(q4 * es_f32(fmaf((float)a, h2, t00), bl, -bl));
                 const int row = r * plane + cb;
+                unsigned wraps = 0u;
 #pragma unroll
-                for (int c = 0; c < W; ++c) tile.add_int(row + c, mulhi_rn(rq, wi[c]), sg);
+                for (int c = 0; c < W; ++c) wraps = tile.add_int_run(row + c, mulhi_rn(rq, wi[c]), wraps);
+                if (wraps) tile.add_carries(row, W, wraps, sg);
             }
         } else {
 #pragma unroll 1
@@ -694,8 +714,10 @@ __device__ __forceinline__ void spread_point_f32(const SpreadArgs &p, const Poin
                 for (int b = 0; b < W; ++b) {
                     const int rq = __float2int_rn(qa * w1[b]);
                     const int line = row + c1[b];
+                    unsigned wraps = 0u;
 #pragma unroll
-                    for (int c = 0; c < W; ++c) tile.add_int(line + c, mulhi_rn(rq, wi[c]), sg);
+                    for (int c = 0; c < W; ++c) wraps = tile.add_int_run(line + c, mulhi_rn(rq, wi[c]), wraps);
+                    if (wraps) tile.add_carries(line, W, wraps, sg);
                 }
             }
         }
