@@ -331,14 +331,78 @@ struct PairData {
 // stride by SMs x threads, often a multiple of N^d) visit every node i instead of one, so the
 // lanes of a warp meet the negligible pairs of the tails of f at the same rate.
 
-// Load pair pr; false when its strength is zero.  ANG: also the unit direction (angular kernels).
+// A position in the pair numbering, advanced by a fixed stride without divisions: pr = t nnode + u
+// and the sheared first node i = (u + t K) mod nnode.  A stride of dt nnode + du moves i by
+// di = (du + dt K) mod nnode, and by K mod nnode more when u wraps.
+struct PairCursor {
+    long long pr;
+    int t, u, i;
+};
+struct PairStep {
+    long long d;
+    int dt, du, di, dk;
+};
+
+__device__ __forceinline__ PairCursor pair_cursor(const SpreadArgs &p, long long pr)
+{
+    PairCursor c;
+    c.pr = pr;
+    c.t = (int)(pr / p.nnode);
+    c.u = (int)(pr - (long long)c.t * p.nnode);
+    c.i = (int)(((long long)c.u + (long long)c.t * kPairShear) % p.nnode);
+    return c;
+}
+
+__device__ __forceinline__ PairStep pair_step(const SpreadArgs &p, long long stride)
+{
+    PairStep s;
+    s.d = stride;
+    s.dt = (int)(stride / p.nnode);
+    s.du = (int)(stride - (long long)s.dt * p.nnode);
+    s.di = (int)(((long long)s.du + (long long)s.dt * kPairShear) % p.nnode);
+    s.dk = (int)(kPairShear % p.nnode);
+    return s;
+}
+
+__device__ __forceinline__ void pair_advance(const SpreadArgs &p, PairCursor &c, const PairStep &s)
+{
+    const int nnode = p.nnode;
+    c.pr += s.d;
+    c.t += s.dt;
+    c.u += s.du;
+    c.i += s.di;
+    if (c.i >= nnode) c.i -= nnode;
+    if (c.u >= nnode) {
+        c.u -= nnode;
+        c.t += 1;
+        c.i += s.dk;
+        if (c.i >= nnode) c.i -= nnode;
+    }
+}
+
+// Axis indices of node k (C order, axis D-1 fastest) from float quotients: (k + 1/2)/N lies at
+// least 1/(2N) from an integer and its FP32 value within 2^-23 (k + 1/2)/N < 1/(4N) of it for
+// k < 2^21 (every node count a plan allows), so the truncation is the exact quotient.
+template <int D>
+__device__ __forceinline__ void node_axes(int k, int N, float invN, int (&ax)[D])
+{
+#pragma unroll
+    for (int l = D - 1; l > 0; --l) {
+        const int q = __float2int_rz(((float)k + 0.5f) * invN);
+        ax[l] = k - q * N;
+        k = q;
+    }
+    ax[0] = k;
+}
+
+// Load the pair at cursor c; false when its strength is zero.  ANG: also the unit direction
+// (angular kernels).
 template <typename T, int D, bool ANG = false>
-__device__ __forceinline__ bool load_pair(const SpreadArgs &p, long long pr, PairData<T, D> &P)
+__device__ __forceinline__ bool load_pair(const SpreadArgs &p, const PairCursor &c, PairData<T, D> &P)
 {
     const int nnode = p.nnode, N = p.N;
-    const int t = (int)(pr / nnode);
-    int i = (int)(pr - (long long)t * nnode);
-    if (2 * t != nnode) i = (int)(((unsigned)i + (unsigned)t * kPairShear) % (unsigned)nnode);
+    const int t = c.t;
+    const int i = (2 * t != nnode) ? c.i : c.u;  // the half row t = nnode/2 is not sheared
     int j = i + t;
     if (j >= nnode) j -= nnode;
     P.mult = t ? T(2) : T(1);
@@ -346,14 +410,15 @@ __device__ __forceinline__ bool load_pair(const SpreadArgs &p, long long pr, Pai
     const T *acoef = static_cast<const T *>(p.a);
     const T aij = acoef[i] * acoef[j];
     if (aij == T(0)) return false;
-    int ii = i, jj = j;
+    const float invN = 1.0f / (float)N;
+    int ai[D], aj[D];
+    node_axes<D>(i, N, invN, ai);
+    node_axes<D>(j, N, invN, aj);
     T g2 = T(0);
 #pragma unroll
     for (int l = D - 1; l >= 0; --l) {
-        const int ni = ii % N, nj = jj % N;
+        const int ni = ai[l], nj = aj[l];
         const T vi = vnode[ni], vj = vnode[nj];
-        ii /= N;
-        jj /= N;
         T dl = vi - vj, sl = vi + vj;
         if constexpr (sizeof(T) == 4) {  // FP32 nodes carry their rounding in a second term
             const float li = p.vnode_lo[ni], lj = p.vnode_lo[nj];
@@ -876,16 +941,16 @@ __device__ __forceinline__ void spread_point_any(const SpreadArgs &p, const Poin
     else spread_point_body<T, D, W, Tile, SLAB>(p, pt, tile, row_lo, nrows, plane);
 }
 
-// Advance pr (in steps of `stride`, below `end`) to this lane's next pair that is not negligible:
+// Advance the cursor c (in steps of st, below `end`) to this lane's next pair that is not negligible:
 // a loaded pair with non-zero strength, a strength bound not below the screening threshold tau
 // (0: no screening), and a bound Ut >= floor_q on every point's |q| in tile units.  On success
 // P.base is multiplied by the pair's multiplicity; false when no pair is left.
 template <typename T, int D, bool ANG>
-__device__ __forceinline__ bool next_pair(const SpreadArgs &p, long long &pr, long long end, long long stride, T sc,
+__device__ __forceinline__ bool next_pair(const SpreadArgs &p, PairCursor &c, long long end, const PairStep &st, T sc,
                                           T tau, T floor_q, PairData<T, D> &P)
 {
-    for (; pr < end; pr += stride) {
-        if (!load_pair<T, D, ANG>(p, pr, P)) continue;
+    for (; c.pr < end; pair_advance(p, c, st)) {
+        if (!load_pair<T, D, ANG>(p, c, P)) continue;
         const T U = pair_bound<T, D>(p, P);
         if (tau > T(0) && U < tau) continue;
         if (U * P.mult * sc * kconst<T>(p).wmax < floor_q) continue;
@@ -915,10 +980,11 @@ template <typename T, int D, int W, typename Tile, bool ANG>
 __device__ __forceinline__ void spread_pairs(const SpreadArgs &p, long long first, long long end, long long stride,
                                              T sc, T tau, T floor_q, const Tile &tile, int row_lo, int nrows, int plane)
 {
-    long long pr = first;
+    PairCursor c = pair_cursor(p, first);
+    const PairStep st = pair_step(p, stride);
     for (;;) {
         PairData<T, D> P;
-        const bool ok = next_pair<T, D, ANG>(p, pr, end, stride, sc, tau, floor_q, P);
+        const bool ok = next_pair<T, D, ANG>(p, c, end, st, sc, tau, floor_q, P);
         if (!__any_sync(0xffffffffu, ok)) break;
         if (!ok) zero_pair<T, D>(P);
         const T qbase = P.base * sc;
@@ -927,7 +993,7 @@ __device__ __forceinline__ void spread_pairs(const SpreadArgs &p, long long firs
             make_point<T, D, ANG>(p, P, qbase, m, pt);
             spread_point_any<T, D, W, Tile, false>(p, pt, tile, row_lo, nrows, plane);
         }
-        if (ok) pr += stride;
+        if (ok) pair_advance(p, c, st);
     }
 }
 
@@ -1095,10 +1161,11 @@ __device__ __forceinline__ void spread_pairs_queued(const SpreadArgs &p, long lo
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     int count = 0;  // queued points, the same in every lane
-    long long pr = first;
+    PairCursor c = pair_cursor(p, first);
+    const PairStep st = pair_step(p, nthr);
     for (;;) {
         PairData<T, D> P;
-        const bool ok = next_pair<T, D, ANG>(p, pr, end, nthr, sc, tau, floor_q, P);
+        const bool ok = next_pair<T, D, ANG>(p, c, end, st, sc, tau, floor_q, P);
         if (!__any_sync(full, ok)) break;
         const T qbase = ok ? P.base * sc : T(0);
         for (int m = 0; m < p.M; ++m) {
@@ -1123,7 +1190,7 @@ __device__ __forceinline__ void spread_pairs_queued(const SpreadArgs &p, long lo
                 count += n;
             }
         }
-        if (ok) pr += nthr;
+        if (ok) pair_advance(p, c, st);
     }
     __syncwarp();
     queue_spread<T, D, W, Tile, SLAB, LATE>(p, buf, lane, lane < count, tile, row_lo, nrows, plane);
