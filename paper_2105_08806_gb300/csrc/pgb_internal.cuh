@@ -211,7 +211,8 @@ cudaError_t launch_recon_last(const double *in, Dims3 in_dims, const double *A, 
 // from pair to pair; the bound gets a 1e-5 margin in k_bound_reduce.
 // vnode32 != nullptr selects FP32 pair terms (the FP32 path).
 // hist != nullptr: also count every pair bound |a_i| Bw |a_j| B_ij prod mu^-2 into the screening histogram.
-cudaError_t launch_loss(const double *a, const double *vnode, const float *vnode32, const float *vnode32_lo, int N,
+cudaError_t launch_loss(const double *a, const float *a32, const double *vnode, const float *vnode32,
+                        const float *vnode32_lo, int N,
                         int d, int M,
                         const double *sig, const double *wsig, const float *sig32, const float *wsig32,
                         const Angular &ang, double angmax, double Wsig, double gamma,

@@ -397,9 +397,9 @@ PG_API int pg_boltz_collide(pg_boltz_plan_t *p, const double *f_dev, double *Q_d
                          "memset grid")))
         return rc;
     ++launches;
-    if ((rc = cuda_check(pgb::launch_loss(p->a64, p->v64, f32 ? p->v32 : nullptr, p->v32lo, N, d, p->M, p->sig64, p->wsig64,
-                                          p->sig32, p->wsig32, p->ang, p->angmax, p->Wsig, p->gamma, p->fast_gamma,
-                                          p->Bconst * p->Wsig, p->inv_mu2, p->S, p->r, p->h, p->ub,
+    if ((rc = cuda_check(pgb::launch_loss(p->a64, f32 ? p->a32 : nullptr, p->v64, f32 ? p->v32 : nullptr, p->v32lo, N,
+                                          d, p->M, p->sig64, p->wsig64, p->sig32, p->wsig32, p->ang, p->angmax,
+                                          p->Wsig, p->gamma, p->fast_gamma, p->Bconst * p->Wsig, p->inv_mu2, p->S, p->r, p->h, p->ub,
                                           p->screen_eps > 0.0 ? p->hist : nullptr, p->stream),
                          "loss")))
         return rc;

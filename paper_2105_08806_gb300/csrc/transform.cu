@@ -97,7 +97,8 @@ constexpr int kLossThreads = 128;
 // in the box |v'_l| <= |c_l| + rad and mu^-2 grows with |v|, so ub_i bounds the spreading
 // strengths sum_{j,m} |q_ijm| (times Bconst, which Bw carries).  PT is the arithmetic of the
 // pair terms: FP64, or FP32 for the FP32 path (node differences with the nodes' FP32 rounding
-// added back); the loss sums are FP64 either way, the bound's 64-term partial sums FP32.
+// added back); the loss sums are FP64 in the FP64 path and float pairs (two-sum, about 2^-44
+// relative) over the FP32 coefficients in the FP32 path, the bound's 64-term partial sums FP32.
 // b(cos theta) summed over the sphere set for the pair direction dvec = v_i - v_j (|dvec| = g):
 // (1/Wsig) sum_m w_m b(dvec . sigma_m / g), cos theta = 0 when g = 0 (Eq. collision_form).
 template <typename PT>
@@ -119,6 +120,7 @@ __device__ __forceinline__ PT angular_mean(const Angular &ang, const PT *dvec, P
 
 template <typename PT>
 __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict__ a,
+                                                        const float *__restrict__ a32,
                                                         const PT *__restrict__ vnode,
                                                         const float *__restrict__ vnode_lo, int N, int d, int M,
                                                         const PT *__restrict__ sig, const PT *__restrict__ wsig,
@@ -150,6 +152,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict_
     const double ai_w = fabs(a[i]) * Bw * angmax;  // pair bound = ai_w * |a_j| B_ij prod mu^-2
     const PT inv_wsig = PT(1.0 / Wsig);
     double acc = 0.0, bnd = 0.0;
+    float as = 0.0f, ac = 0.0f;  // FP32 plans: the pair terms' sum as as + ac
     for (int j0 = threadIdx.x * 64; j0 < nnode; j0 += blockDim.x * 64) {
         PT bp = PT(0);
         const int j1 = min(j0 + 64, nnode);
@@ -172,12 +175,25 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict_
             case 2: B = sqrt(g); break;
             default: B = (g2 > PT(0)) ? pow(g, gam) : PT(0); break;
             }
-            const PT aj = PT(a[j]);
-            // the pair term in PT, its sum in FP64 (the batched plans' loss sums the same way)
-            if (ang.n)
+            PT aj;
+            if (ang.n) {  // the pair term in PT, its sum in FP64
+                aj = PT(a[j]);
                 acc = fma(double(B * angular_mean<PT>(ang, dv, g, d, M, sig, wsig, inv_wsig)), a[j], acc);
-            else
+            } else if constexpr (sizeof(PT) == 4) {
+                // FP32: the FP32 coefficient the spreading uses, and the product's exact value
+                // (FMA residual) summed as an unevaluated pair of floats (two-sum): no FP64
+                // operation per pair, about 2^-44 relative
+                aj = a32[j];
+                const float pt = B * aj;
+                const float pe = fmaf(B, aj, -pt);
+                const float t = as + pt;
+                const float bv = t - as;
+                ac += ((as - (t - bv)) + (pt - bv)) + pe;
+                as = t;
+            } else {
+                aj = PT(a[j]);
                 acc = fma(double(B), a[j], acc);
+            }
             if (aj != PT(0) && B != PT(0)) {
                 PT mu = PT(1);
                 for (int l = 0; l < d; ++l) {
@@ -191,6 +207,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict_
         }
         bnd += (double)bp;
     }
+    acc += (double)as + (double)ac;
     const double tot = block_sum<kLossThreads>(acc);
     const double tb = block_sum<kLossThreads>(bnd);
     if (threadIdx.x == 0) {
@@ -461,7 +478,8 @@ cudaError_t launch_recon_last(const double *in, Dims3 in_dims, const double *A, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_loss(const double *a, const double *vnode, const float *vnode32, const float *vnode32_lo, int N,
+cudaError_t launch_loss(const double *a, const float *a32, const double *vnode, const float *vnode32,
+                        const float *vnode32_lo, int N,
                         int d, int M,
                         const double *sig, const double *wsig, const float *sig32, const float *wsig32,
                         const Angular &ang, double angmax, double Wsig, double gamma,
@@ -470,10 +488,10 @@ cudaError_t launch_loss(const double *a, const double *vnode, const float *vnode
 {
     const int nnode = (d == 2) ? N * N : N * N * N;
     if (vnode32)
-        k_loss<float><<<nnode, kLossThreads, 0, s>>>(a, vnode32, vnode32_lo, N, d, M, sig32, wsig32, ang, angmax, Wsig,
+        k_loss<float><<<nnode, kLossThreads, 0, s>>>(a, a32, vnode32, vnode32_lo, N, d, M, sig32, wsig32, ang, angmax, Wsig,
                                                      gamma, fast_gamma, Bw, inv_mu2, S, r, h, ub, hist);
     else
-        k_loss<double><<<nnode, kLossThreads, 0, s>>>(a, vnode, nullptr, N, d, M, sig, wsig, ang, angmax, Wsig, gamma,
+        k_loss<double><<<nnode, kLossThreads, 0, s>>>(a, nullptr, vnode, nullptr, N, d, M, sig, wsig, ang, angmax, Wsig, gamma,
                                                       fast_gamma, Bw, inv_mu2, S, r, h, ub, hist);
     return cudaGetLastError();
 }
