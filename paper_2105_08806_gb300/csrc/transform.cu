@@ -153,16 +153,27 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict_
     const PT inv_wsig = PT(1.0 / Wsig);
     double acc = 0.0, bnd = 0.0;
     float as = 0.0f, ac = 0.0f;  // FP32 plans: the pair terms' sum as as + ac
-    for (int j0 = threadIdx.x * 64; j0 < nnode; j0 += blockDim.x * 64) {
-        PT bp = PT(0);
-        const int j1 = min(j0 + 64, nnode);
-        for (int j = j0; j < j1; ++j) {
-            int t = j;
+    const float invN = 1.0f / (float)N;
+    // every thread takes nodes j = threadIdx.x + k blockDim.x; the bound's FP32 partial sums run
+    // over 64 terms at most
+    PT bp = PT(0);
+    int nb = 0;
+    for (int j = threadIdx.x; j < nnode; j += blockDim.x) {
+        {
+            // axis indices of node j (C order) from float quotients: (t + 1/2)/N lies at least
+            // 1/(2N) from an integer and its FP32 value within 2^-23 (t + 1/2)/N < 1/(4N) of it
+            // (nnode <= 2^21), so the truncation is the exact quotient
+            int jl[3], t = j;
+            for (int l = d - 1; l > 0; --l) {
+                const int qt = __float2int_rz(((float)t + 0.5f) * invN);
+                jl[l] = t - qt * N;
+                t = qt;
+            }
+            jl[0] = t;
             PT g2 = PT(0), vj[3] = {PT(0), PT(0), PT(0)}, dv[3] = {PT(0), PT(0), PT(0)};
-            for (int l = d - 1; l >= 0; --l) {
-                const int nj = t % N;
+            for (int l = 0; l < d; ++l) {
+                const int nj = jl[l];
                 vj[l] = vnode[nj];
-                t /= N;
                 dv[l] = vi[l] - vj[l];
                 if (vnode_lo) dv[l] += vil[l] - PT(vnode_lo[nj]);  // FP32 nodes: their rounding, too
                 g2 += dv[l] * dv[l];
@@ -205,8 +216,13 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict_
                 if (hist) atomicAdd(&s_hist[screen_bin(ai_w * (double)u)], 1u);
             }
         }
-        bnd += (double)bp;
+        if (++nb == 64) {
+            bnd += (double)bp;
+            bp = PT(0);
+            nb = 0;
+        }
     }
+    bnd += (double)bp;
     acc += (double)as + (double)ac;
     const double tot = block_sum<kLossThreads>(acc);
     const double tb = block_sum<kLossThreads>(bnd);
