@@ -21,28 +21,49 @@ __device__ __forceinline__ long long stride_of(const Dims3 &d, int ax)
     return ax == 2 ? 1LL : (ax == 1 ? (long long)d.e[2] : (long long)d.e[1] * d.e[2]);
 }
 
+// The separable passes and the final combine split each output's dot product over kSplit lanes
+// of a warp (lane g takes terms g, g + kSplit, ...) and add the partial sums by a butterfly of
+// shuffles, in a fixed order: the outputs are few (thousands) and their dot products long
+// (n/2 + 1 terms), so one thread per output left most SMs idle behind a serial chain of FMAs.
+constexpr int kSplit = 8;
+
+__device__ __forceinline__ double split_sum(double v)
+{
+#pragma unroll
+    for (int off = kSplit / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
 __global__ void k_axis_pass(const double *__restrict__ in, Dims3 id, int ax,
                             const double *__restrict__ A, int m, double *__restrict__ out)
 {
     Dims3 od = id;
     od.e[ax] = m;
     const long long total = (long long)od.e[0] * od.e[1] * od.e[2];
+    const long long tlanes = total * kSplit;
     const int len = id.e[ax];
     const long long sax = stride_of(id, ax);
-    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < total;
-         o += (long long)gridDim.x * blockDim.x) {
-        int oc[3];
-        oc[2] = (int)(o % od.e[2]);
-        const long long t = o / od.e[2];
-        oc[1] = (int)(t % od.e[1]);
-        oc[0] = (int)(t / od.e[1]);
-        const int k = oc[ax];
-        oc[ax] = 0;
-        const long long base = ((long long)oc[0] * id.e[1] + oc[1]) * id.e[2] + oc[2];
-        const double *arow = A + (long long)k * len;
+    const int lane = threadIdx.x & 31;
+    // every lane of a warp runs the same iterations (the shuffles need the whole warp)
+    for (long long tt = blockIdx.x * (long long)blockDim.x + threadIdx.x; tt - lane < tlanes;
+         tt += (long long)gridDim.x * blockDim.x) {
+        const long long o = tt / kSplit;
+        const int g = (int)(tt % kSplit);
         double acc = 0.0;
-        for (int s = 0; s < len; ++s) acc = fma(arow[s], in[base + s * sax], acc);
-        out[o] = acc;
+        if (tt < tlanes) {
+            int oc[3];
+            oc[2] = (int)(o % od.e[2]);
+            const long long t = o / od.e[2];
+            oc[1] = (int)(t % od.e[1]);
+            oc[0] = (int)(t / od.e[1]);
+            const int k = oc[ax];
+            oc[ax] = 0;
+            const long long base = ((long long)oc[0] * id.e[1] + oc[1]) * id.e[2] + oc[2];
+            const double *arow = A + (long long)k * len;
+            for (int s = g; s < len; s += kSplit) acc = fma(arow[s], in[base + s * sax], acc);
+        }
+        acc = split_sum(acc);
+        if (tt < tlanes && g == 0) out[o] = acc;
     }
 }
 
@@ -277,23 +298,30 @@ __global__ void k_axis_pass_fixed(const unsigned long long *__restrict__ in, Dim
     Dims3 od = id;
     od.e[ax] = m;
     const long long total = (long long)od.e[0] * od.e[1] * od.e[2];
+    const long long tlanes = total * kSplit;
     const int len = id.e[ax];
     const long long sax = stride_of(id, ax);
     const double unit = ldexp(scale, -global_exponent(*Bp));
-    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < total;
-         o += (long long)gridDim.x * blockDim.x) {
-        int oc[3];
-        oc[2] = (int)(o % od.e[2]);
-        const long long t = o / od.e[2];
-        oc[1] = (int)(t % od.e[1]);
-        oc[0] = (int)(t / od.e[1]);
-        const int k = oc[ax];
-        oc[ax] = 0;
-        const long long base = ((long long)oc[0] * id.e[1] + oc[1]) * id.e[2] + oc[2];
-        const double *arow = A + (long long)k * len;
+    const int lane = threadIdx.x & 31;
+    for (long long tt = blockIdx.x * (long long)blockDim.x + threadIdx.x; tt - lane < tlanes;
+         tt += (long long)gridDim.x * blockDim.x) {
+        const long long o = tt / kSplit;
+        const int g = (int)(tt % kSplit);
         double acc = 0.0;
-        for (int s = 0; s < len; ++s) acc = fma(arow[s], (double)(long long)in[base + s * sax], acc);
-        out[o] = acc * unit;
+        if (tt < tlanes) {
+            int oc[3];
+            oc[2] = (int)(o % od.e[2]);
+            const long long t = o / od.e[2];
+            oc[1] = (int)(t % od.e[1]);
+            oc[0] = (int)(t / od.e[1]);
+            const int k = oc[ax];
+            oc[ax] = 0;
+            const long long base = ((long long)oc[0] * id.e[1] + oc[1]) * id.e[2] + oc[2];
+            const double *arow = A + (long long)k * len;
+            for (int s = g; s < len; s += kSplit) acc = fma(arow[s], (double)(long long)in[base + s * sax], acc);
+        }
+        acc = split_sum(acc);
+        if (tt < tlanes && g == 0) out[o] = acc * unit;
     }
 }
 
@@ -302,22 +330,32 @@ __global__ void k_final(const double *__restrict__ G, Dims3 gd, const double *__
                         double *__restrict__ Q, double *__restrict__ Qplus, double *__restrict__ Qcopy)
 {
     const long long total = (long long)gd.e[0] * gd.e[1] * m;
+    const long long tlanes = total * kSplit;
     const int lg = gd.e[2];
     const int lh = hd.e[2];
-    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < total;
-         o += (long long)gridDim.x * blockDim.x) {
-        const int o2 = (int)(o % m);
-        const long long row = o / m;
-        const double *gsrc = G + row * lg;
-        const double *hsrc = H + row * lh;
-        const double *drow = D + (long long)o2 * lg;
-        const double *erow = E + (long long)o2 * lh;
+    const int lane = threadIdx.x & 31;
+    for (long long tt = blockIdx.x * (long long)blockDim.x + threadIdx.x; tt - lane < tlanes;
+         tt += (long long)gridDim.x * blockDim.x) {
+        const long long o = tt / kSplit;
+        const int g = (int)(tt % kSplit);
         double qp = 0.0, qm = 0.0;
-        for (int s = 0; s < lg; ++s) qp = fma(drow[s], gsrc[s], qp);
-        for (int s = 0; s < lh; ++s) qm = fma(erow[s], hsrc[s], qm);
-        Qplus[o] = qp;
-        Q[o] = qp - qm;
-        Qcopy[o] = qp - qm;
+        if (tt < tlanes) {
+            const int o2 = (int)(o % m);
+            const long long row = o / m;
+            const double *gsrc = G + row * lg;
+            const double *hsrc = H + row * lh;
+            const double *drow = D + (long long)o2 * lg;
+            const double *erow = E + (long long)o2 * lh;
+            for (int s = g; s < lg; s += kSplit) qp = fma(drow[s], gsrc[s], qp);
+            for (int s = g; s < lh; s += kSplit) qm = fma(erow[s], hsrc[s], qm);
+        }
+        qp = split_sum(qp);
+        qm = split_sum(qm);
+        if (tt < tlanes && g == 0) {
+            Qplus[o] = qp;
+            Q[o] = qp - qm;
+            Qcopy[o] = qp - qm;
+        }
     }
 }
 
@@ -481,8 +519,8 @@ cudaError_t launch_axis_pass(const double *in, Dims3 in_dims, int ax, const doub
 {
     Dims3 od = in_dims;
     od.e[ax] = m;
-    k_axis_pass<<<grid_for((long long)od.e[0] * od.e[1] * od.e[2]), kThreads, 0, s>>>(in, in_dims, ax,
-                                                                                     A, m, out);
+    k_axis_pass<<<grid_for((long long)od.e[0] * od.e[1] * od.e[2] * kSplit), kThreads, 0, s>>>(in, in_dims,
+                                                                                              ax, A, m, out);
     return cudaGetLastError();
 }
 
@@ -504,11 +542,11 @@ cudaError_t launch_loss(const double *a, const float *a32, const double *vnode, 
 {
     const int nnode = (d == 2) ? N * N : N * N * N;
     if (vnode32)
-        k_loss<float><<<nnode, kLossThreads, 0, s>>>(a, a32, vnode32, vnode32_lo, N, d, M, sig32, wsig32, ang, angmax, Wsig,
-                                                     gamma, fast_gamma, Bw, inv_mu2, S, r, h, ub, hist);
+        k_loss<float><<<nnode, kLossThreads, 0, s>>>(a, a32, vnode32, vnode32_lo, N, d, M, sig32, wsig32, ang, angmax,
+                                                     Wsig, gamma, fast_gamma, Bw, inv_mu2, S, r, h, ub, hist);
     else
-        k_loss<double><<<nnode, kLossThreads, 0, s>>>(a, nullptr, vnode, nullptr, N, d, M, sig, wsig, ang, angmax, Wsig, gamma,
-                                                      fast_gamma, Bw, inv_mu2, S, r, h, ub, hist);
+        k_loss<double><<<nnode, kLossThreads, 0, s>>>(a, nullptr, vnode, nullptr, N, d, M, sig, wsig, ang, angmax,
+                                                      Wsig, gamma, fast_gamma, Bw, inv_mu2, S, r, h, ub, hist);
     return cudaGetLastError();
 }
 
@@ -524,8 +562,8 @@ cudaError_t launch_axis_pass_fixed(const unsigned long long *in, Dims3 in_dims, 
 {
     Dims3 od = in_dims;
     od.e[ax] = m;
-    k_axis_pass_fixed<<<grid_for((long long)od.e[0] * od.e[1] * od.e[2]), kThreads, 0, s>>>(in, in_dims, ax, A,
-                                                                                           m, B, scale, out);
+    k_axis_pass_fixed<<<grid_for((long long)od.e[0] * od.e[1] * od.e[2] * kSplit), kThreads, 0, s>>>(
+        in, in_dims, ax, A, m, B, scale, out);
     return cudaGetLastError();
 }
 
@@ -533,9 +571,8 @@ cudaError_t launch_final(const double *G, Dims3 g_dims, const double *D, const d
                          Dims3 h_dims, const double *E, int m, double *Q, double *Qplus,
                          double *Qcopy, cudaStream_t s)
 {
-    k_final<<<grid_for((long long)g_dims.e[0] * g_dims.e[1] * m), kThreads, 0, s>>>(G, g_dims, D, H,
-                                                                                   h_dims, E, m, Q,
-                                                                                   Qplus, Qcopy);
+    k_final<<<grid_for((long long)g_dims.e[0] * g_dims.e[1] * m * kSplit), kThreads, 0, s>>>(G, g_dims, D, H, h_dims,
+                                                                                            E, m, Q, Qplus, Qcopy);
     return cudaGetLastError();
 }
 
