@@ -139,11 +139,11 @@ __device__ __forceinline__ PT angular_mean(const Angular &ang, const PT *dvec, P
     return acc * inv_wsig;
 }
 
-template <typename PT>
+template <typename PT, int D>
 __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict__ a,
                                                         const float *__restrict__ a32,
                                                         const PT *__restrict__ vnode,
-                                                        const float *__restrict__ vnode_lo, int N, int d, int M,
+                                                        const float *__restrict__ vnode_lo, int N, int M,
                                                         const PT *__restrict__ sig, const PT *__restrict__ wsig,
                                                         const Angular ang, double angmax, double Wsig,
                                                         double gamma, int fast_gamma, double Bw,
@@ -155,6 +155,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict_
     if (hist)
         for (int k = threadIdx.x; k < kScreenBins; k += blockDim.x) s_hist[k] = 0u;
     __syncthreads();
+    constexpr int d = D;
     const int nnode = (d == 2) ? N * N : N * N * N;
     const int i = blockIdx.x;
     int idx[3] = {0, 0, 0};
@@ -174,24 +175,26 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict_
     const PT inv_wsig = PT(1.0 / Wsig);
     double acc = 0.0, bnd = 0.0;
     float as = 0.0f, ac = 0.0f;  // FP32 plans: the pair terms' sum as as + ac
-    const float invN = 1.0f / (float)N;
-    // every thread takes nodes j = threadIdx.x + k blockDim.x; the bound's FP32 partial sums run
-    // over 64 terms at most
+    // every thread takes nodes j = threadIdx.x + k blockDim.x, whose axis indices (C order, base N
+    // digits) advance by the step's digits with carries; the bound's FP32 partial sums run over 64
+    // terms at most
+    int jl[D], sl[D];
+    {
+        int t = threadIdx.x, u = blockDim.x;
+#pragma unroll
+        for (int l = D - 1; l >= 0; --l) {
+            jl[l] = t % N;
+            t /= N;
+            sl[l] = u % N;
+            u /= N;
+        }
+    }
     PT bp = PT(0);
     int nb = 0;
     for (int j = threadIdx.x; j < nnode; j += blockDim.x) {
         {
-            // axis indices of node j (C order) from float quotients: (t + 1/2)/N lies at least
-            // 1/(2N) from an integer and its FP32 value within 2^-23 (t + 1/2)/N < 1/(4N) of it
-            // (nnode <= 2^21), so the truncation is the exact quotient
-            int jl[3], t = j;
-            for (int l = d - 1; l > 0; --l) {
-                const int qt = __float2int_rz(((float)t + 0.5f) * invN);
-                jl[l] = t - qt * N;
-                t = qt;
-            }
-            jl[0] = t;
             PT g2 = PT(0), vj[3] = {PT(0), PT(0), PT(0)}, dv[3] = {PT(0), PT(0), PT(0)};
+#pragma unroll
             for (int l = 0; l < d; ++l) {
                 const int nj = jl[l];
                 vj[l] = vnode[nj];
@@ -228,6 +231,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict_
             }
             if (aj != PT(0) && B != PT(0)) {
                 PT mu = PT(1);
+#pragma unroll
                 for (int l = 0; l < d; ++l) {
                     const PT R = fabs(PT(0.5) * (vi[l] + vj[l])) + PT(0.5) * g;
                     mu *= (r == 1) ? (Sp * Sp + R * R) * invS : Sp * cosh(R * invS);
@@ -241,6 +245,13 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const double *__restrict_
             bnd += (double)bp;
             bp = PT(0);
             nb = 0;
+        }
+        int carry = 0;
+#pragma unroll
+        for (int l = D - 1; l >= 0; --l) {
+            jl[l] += sl[l] + carry;
+            carry = jl[l] >= N;
+            if (carry) jl[l] -= N;
         }
     }
     bnd += (double)bp;
@@ -541,12 +552,18 @@ cudaError_t launch_loss(const double *a, const float *a32, const double *vnode, 
                         double *ub, unsigned long long *hist, cudaStream_t s)
 {
     const int nnode = (d == 2) ? N * N : N * N * N;
-    if (vnode32)
-        k_loss<float><<<nnode, kLossThreads, 0, s>>>(a, a32, vnode32, vnode32_lo, N, d, M, sig32, wsig32, ang, angmax,
-                                                     Wsig, gamma, fast_gamma, Bw, inv_mu2, S, r, h, ub, hist);
+    if (vnode32 && d == 2)
+        k_loss<float, 2><<<nnode, kLossThreads, 0, s>>>(a, a32, vnode32, vnode32_lo, N, M, sig32, wsig32, ang, angmax,
+                                                        Wsig, gamma, fast_gamma, Bw, inv_mu2, S, r, h, ub, hist);
+    else if (vnode32)
+        k_loss<float, 3><<<nnode, kLossThreads, 0, s>>>(a, a32, vnode32, vnode32_lo, N, M, sig32, wsig32, ang, angmax,
+                                                        Wsig, gamma, fast_gamma, Bw, inv_mu2, S, r, h, ub, hist);
+    else if (d == 2)
+        k_loss<double, 2><<<nnode, kLossThreads, 0, s>>>(a, nullptr, vnode, nullptr, N, M, sig, wsig, ang, angmax,
+                                                         Wsig, gamma, fast_gamma, Bw, inv_mu2, S, r, h, ub, hist);
     else
-        k_loss<double><<<nnode, kLossThreads, 0, s>>>(a, nullptr, vnode, nullptr, N, d, M, sig, wsig, ang, angmax,
-                                                      Wsig, gamma, fast_gamma, Bw, inv_mu2, S, r, h, ub, hist);
+        k_loss<double, 3><<<nnode, kLossThreads, 0, s>>>(a, nullptr, vnode, nullptr, N, M, sig, wsig, ang, angmax,
+                                                         Wsig, gamma, fast_gamma, Bw, inv_mu2, S, r, h, ub, hist);
     return cudaGetLastError();
 }
 
