@@ -155,7 +155,7 @@ __device__ double block_reduce_sum(double v, double *warp_part)
 // One block per cell: a_i, h_i and the strength bound B_c (same formulas as k_recon_last,
 // k_loss and k_bound_reduce of the single-plan path).  PT is the arithmetic of the pair
 // distances and |v_i - v_j|^gamma (float for FP32 plans; sums are FP64 either way).
-template <typename PT>
+template <typename PT, int D>
 __global__ void __launch_bounds__(kPrepThreads) k_batch_prep(const __grid_constant__ BatchArgs b)
 {
     __shared__ double warp_part[kPrepThreads / 32];
@@ -164,7 +164,8 @@ __global__ void __launch_bounds__(kPrepThreads) k_batch_prep(const __grid_consta
     for (int k = threadIdx.x; k < kScreenBins; k += blockDim.x) s_hist[k] = 0u;
     const int c = blockIdx.x;
     const CellDesc cd = b.cells[c];
-    const int d = b.d, N = cd.N, nnode = cd.nnode;
+    constexpr int d = D;
+    const int N = cd.N, nnode = cd.nnode;
     double *s1 = b.scratch + cd.s_off, *s2 = s1 + cd.s_len;
     const double *R = b.R + cd.R_off;
     // 1. reconstruction: leading passes, then the last axis with a_i = W_i mu_i^2 P_i
@@ -207,30 +208,41 @@ __global__ void __launch_bounds__(kPrepThreads) k_batch_prep(const __grid_consta
     const PT S = PT(cd.S), invS = PT(1) / S, gam = PT(cd.gamma);
     double bsum = 0.0;
     for (int i = threadIdx.x; i < nnode; i += blockDim.x) {
-        int idx[3] = {0, 0, 0}, t = i;
+        int idx[D], t = i;
+#pragma unroll
         for (int l = d - 1; l >= 0; --l) {
             idx[l] = t % N;
             t /= N;
         }
-        PT vi[3], vil[3] = {PT(0), PT(0), PT(0)};
-        for (int l = 0; l < 3; ++l) vi[l] = (l < d) ? vn[idx[l]] : PT(0);
-        if (vlo)
-            for (int l = 0; l < d; ++l) vil[l] = PT(vlo[idx[l]]);
+        PT vi[D], vil[D];
+#pragma unroll
+        for (int l = 0; l < d; ++l) {
+            vi[l] = vn[idx[l]];
+            vil[l] = vlo ? PT(vlo[idx[l]]) : PT(0);
+        }
         double L = 0.0, U = 0.0;
+        float Ls = 0.0f, Lc = 0.0f;  // FP32 plans: the loss terms' sum as Ls + Lc (two-sum)
+        int jl[D];                   // axis indices of node j (C order), advanced with carries
+#pragma unroll
+        for (int l = 0; l < d; ++l) jl[l] = 0;
         for (int j0 = 0; j0 < nnode; j0 += 64) {
             PT Up = PT(0);  // bound: partial sums of 64 terms, then FP64
             const int j1 = min(j0 + 64, nnode);
             for (int j = j0; j < j1; ++j) {
-                int u = j;
                 PT g2 = PT(0), mu = PT(1);
-                PT vj[3];
-                for (int l = d - 1; l >= 0; --l) {
-                    const int nj = u % N;
+                PT vj[D];
+#pragma unroll
+                for (int l = 0; l < d; ++l) {
+                    const int nj = jl[l];
                     vj[l] = vn[nj];
-                    u /= N;
                     PT dl = vi[l] - vj[l];
                     if (vlo) dl += vil[l] - PT(vlo[nj]);
                     g2 += dl * dl;
+                }
+#pragma unroll
+                for (int l = d - 1; l >= 0; --l) {  // next node
+                    if (++jl[l] < N) break;
+                    jl[l] = 0;
                 }
                 const PT g = sqrt(g2);
                 PT B;
@@ -240,8 +252,20 @@ __global__ void __launch_bounds__(kPrepThreads) k_batch_prep(const __grid_consta
                 case 2: B = sqrt(g); break;
                 default: B = (g2 > PT(0)) ? pow(g, gam) : PT(0); break;
                 }
-                const PT aj = PT(a[j]);
-                L = fma(double(B), a[j], L);  // as the single-plan loss kernel
+                PT aj;
+                if constexpr (sizeof(PT) == 4) {  // as the single-plan loss kernel
+                    aj = af[j];
+                    const float pt = B * aj;
+                    const float pe = fmaf(B, aj, -pt);
+                    const float tt = Ls + pt;
+                    const float bv = tt - Ls;
+                    Lc += ((Ls - (tt - bv)) + (pt - bv)) + pe;
+                    Ls = tt;
+                } else {
+                    aj = PT(a[j]);
+                    L = fma(double(B), a[j], L);
+                }
+#pragma unroll
                 for (int l = 0; l < d; ++l) {
                     const PT R_ = fabs(PT(0.5) * (vi[l] + vj[l])) + PT(0.5) * g;
                     mu *= (b.r == 1) ? (S * S + R_ * R_) * invS : S * cosh(R_ * invS);
@@ -252,6 +276,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_batch_prep(const __grid_consta
             }
             U += (double)Up;
         }
+        L += (double)Ls + (double)Lc;
         double scl = 1.0;
         for (int l = 0; l < d; ++l) scl *= im[idx[l]];
         b.h[cd.a_off + i] = a[i] * Bw * L * scl;
@@ -621,8 +646,10 @@ int enqueue_batch(pg_boltz_plan_t *p, cudaStream_t s, const double *f, double *Q
     if ((rc = cuda_check(cudaMemsetAsync(a.counter, 0, 256 + (size_t)B.grid_cells * 8, s), "memset grids")))
         return rc;
     const bool f32 = (B.prec == PG_PREC_FP32);
-    if (f32) pgb::k_batch_prep<float><<<B.ncell, pgb::kPrepThreads, 0, s>>>(a);
-    else pgb::k_batch_prep<double><<<B.ncell, pgb::kPrepThreads, 0, s>>>(a);
+    if (f32 && B.d == 2) pgb::k_batch_prep<float, 2><<<B.ncell, pgb::kPrepThreads, 0, s>>>(a);
+    else if (f32) pgb::k_batch_prep<float, 3><<<B.ncell, pgb::kPrepThreads, 0, s>>>(a);
+    else if (B.d == 2) pgb::k_batch_prep<double, 2><<<B.ncell, pgb::kPrepThreads, 0, s>>>(a);
+    else pgb::k_batch_prep<double, 3><<<B.ncell, pgb::kPrepThreads, 0, s>>>(a);
     if ((rc = cuda_check(cudaGetLastError(), "batched prep"))) return rc;
     if ((rc = cuda_check(pgb::batch_spread_launch(f32, B.d, B.w, a, B.spread_blocks, B.spread_threads, B.spread_smem, s),
                          "batched spread")))
