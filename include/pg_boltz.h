@@ -49,8 +49,9 @@ extern "C" {
 /* Arithmetic of the spreading stage. */
 #define PG_PREC_AUTO 0 /* tol < 1e-8 -> FP64, else FP32                          */
 #define PG_PREC_FP64 1 /* FP64 point generation, spreading and transform         */
-#define PG_PREC_FP32 2 /* FP32 point generation and shared-memory spreading;
-                          FP64 global grid, cosine transform, deconvolution, loss */
+#define PG_PREC_FP32 2 /* FP32 point generation and shared-memory spreading (exact
+                          integer sums), FP32 loss pair terms summed as float pairs;
+                          FP64 global grid, cosine transform, deconvolution, moments */
 
 /* Sphere quadrature for d = 3 (d = 2 always uses M uniform polar angles, Section 4.1). */
 #define PG_SPHERE_AUTO 0      /* antipodal Fibonacci set (M even)                  */
