@@ -38,7 +38,8 @@
 //    Et = Eg - tile_bits(d), plus per-cell carry counters in a per-block global array (SplitTile):
 //    the cell's value is word + 2^32 carry.  A contribution goes to its word with one native 32-bit
 //    shared atomic, and only an addition that overflows the word's signed range (seen from the
-//    returned old value) moves the cell's carry counter.  (Floating-point shared atomics are
+//    returned old value) moves the cell's carry counter; the wraps of a run of w cells are
+//    collected in a register mask and their carries added after the run.  (Floating-point shared atomics are
 //    compare-and-swap loops and their rounding limits FP32 accuracy; 64-bit integer shared atomics
 //    are several times slower than 32-bit ones.)  Points below 2^29 tile units -- nearly all of
 //    them -- form their contributions in integers: the row factor 4 q psi_a (psi_b) and the column
@@ -47,9 +48,10 @@
 //    word + 2^32 carry (scaled by 2^tile_bits(d)) to the global grid.  Each contribution is rounded
 //    to the tile unit (at most about one unit); all later additions are exact.
 //
-// Negligible pairs: a pair whose strength bound keeps every one of its points below 0.1 tile unit
-// (FP64: 0.49 grid unit) adds exactly zero (every contribution rounds to zero), so the kernels
-// skip it, and points below that bound are skipped one by one.  Each lane searches ahead for its
+// Negligible pairs: in the FP32 kernels a pair whose strength bound keeps every one of its points
+// below 0.1 tile unit adds exactly zero (every contribution rounds to zero), so it is skipped, and
+// so are such points one by one; the FP64 kernels skip pairs whose summed bounds stay below
+// 2^-64 B (2^-3 grid units in all).  Each lane searches ahead for its
 // next pair that is not negligible, so that the lanes of a warp spread real pairs together (with
 // the node sets of the workloads here, 25-75% of all pairs lie in the tails of f and are skipped).
 #pragma once
